@@ -1,0 +1,443 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check is a closed form,
+an exact discrete invariant of the scheme, a published value, or a library
+routine that computes the same special function another way.  A dropped term,
+a wrong sign or index, or a transposed operand in the oracle fails at least
+one of them (see the comment on each test).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.special as sp
+from scipy import integrate
+
+import oracle.oracle as o
+from paper_1610_06749_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+MU, DD, ALPHA = (1.73, 1.87), (0.037, 0.037), 1.6e-6
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------
+# seeded inputs
+# --------------------------------------------------------------------------
+
+def test_splitmix64_published_vectors():
+    g = _gold("splitmix64.json")["vectors"]
+    got0 = [format(int(v), "016x") for v in synth.splitmix64(g[0]["seed"], 3)]
+    assert got0 == g[0]["outputs_hex"]
+    got1 = [str(int(v)) for v in synth.splitmix64(g[1]["seed"], 3)]
+    assert got1 == g[1]["outputs_dec"]
+
+
+def test_uniform_tracks_are_reproducible_and_in_range():
+    a = synth.uniform_tracks(42, 500, 0.1, 0.2, 1e-3)
+    b = synth.uniform_tracks(42, 500, 0.1, 0.2, 1e-3)
+    assert np.array_equal(a.x_cm, b.x_cm) and np.array_equal(a.let_keV_um, b.let_keV_um)
+    assert a.x_cm.min() >= 0 and a.x_cm.max() < 0.1 and a.y_cm.max() < 0.2
+    assert a.let_keV_um.min() >= 1.0 and a.let_keV_um.max() < 1000.0
+
+
+def test_poisson_arrival_count_matches_rate():
+    # mean count lambda*T with lambda = rate*Lx*Ly; 5 sigma band
+    rate, L, dt, n = 1e7, 0.05, 1e-8, 20000
+    tr = synth.poisson_tracks(7, rate, L, L, dt, n, 1e-3, synth.CONTINUOUS_LET)
+    lam_T = rate * L * L * dt * n
+    assert abs(len(tr) - lam_T) < 5 * math.sqrt(lam_T)
+    assert np.all(np.diff(tr.step) >= 0) and tr.step.max() < n
+    frac20 = np.mean(tr.let_keV_um == 20.0)
+    assert abs(frac20 - 0.7) < 5 * math.sqrt(0.21 / len(tr))
+
+
+# --------------------------------------------------------------------------
+# closed forms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("x", [1e-6, 1e-3, 0.1, 1.0, 5.0, 20.0, 39.9, 40.1, 80.0, 300.0])
+def test_ei_matches_scipy_expi(x):
+    # own series / asymptotic code vs an independent library implementation
+    ref = sp.expi(x) * math.exp(-x)
+    assert o.ei_scaled(x) == pytest.approx(ref, rel=2e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("let", [1e-3, 0.03, 0.115, 1.02, 10.0, 100.0, 1000.0])
+def test_jaffe_printed_form_equals_integral_form(let):
+    # Eq. (Jaffe_noangle) through Ei vs its integral representation
+    E = 2000.0
+    a = o.jaffe_parallel(let, 1e-3, 0.2, E, 1.73, 0.0356, ALPHA, method="ei")
+    b = o.jaffe_parallel(let, 1e-3, 0.2, E, 1.73, 0.0356, ALPHA, method="quad")
+    assert a == pytest.approx(b, rel=1e-10)
+    assert 0.0 < a <= 1.0
+
+
+def test_jaffe_limits():
+    # y1 -> infinity (no recombination): f -> 1; the integral is bounded by
+    # its end-point values: 1/(1 + ln(1+y2)/y1) <= f <= 1
+    f = o.jaffe_parallel(1e-6, 1e-3, 0.02, 1e4, 1.8, 0.037, ALPHA)
+    assert f == pytest.approx(1.0, abs=1e-6)
+    y1, y2 = o.jaffe_y(10.0, 1e-3, 0.02, 1e4, 1.8, 0.037, ALPHA)
+    f = o.jaffe_parallel(10.0, 1e-3, 0.02, 1e4, 1.8, 0.037, ALPHA)
+    assert 1.0 / (1.0 + math.log1p(y2) / y1) <= f <= 1.0
+
+
+def test_jaffe_config1_value_and_paper_table_ions():
+    # y1 = 8 pi D/(alpha N0), y2 = 2 d D/(mu b^2 E) for 100 keV/um, b = 10 um,
+    # d = 200 um, 200 V, mean mu 1.80, D 0.037
+    y1, y2 = o.jaffe_y(100.0, 1e-3, 0.02, 1e4, 1.80, 0.037, ALPHA)
+    N0 = 100.0 * 1e7 / 34.0
+    assert y1 == pytest.approx(8 * math.pi * 0.037 / (ALPHA * N0), rel=1e-14)
+    assert y1 == pytest.approx(0.019761, rel=1e-4) and y2 == pytest.approx(0.082222, rel=1e-4)
+    assert o.jaffe_parallel(100.0, 1e-3, 0.02, 1e4, 1.80, 0.037, ALPHA) == pytest.approx(0.39835, abs=5e-6)
+
+
+def test_jaffe_angle_uses_modified_bessel_identity():
+    # (i pi/2) H0^(1)(iZ) = K0(Z) for real Z > 0 (Eq. angle)
+    for Z in [0.1, 1.0, 7.5]:
+        h = (1j * math.pi / 2) * sp.hankel1(0, 1j * Z)
+        assert h.real == pytest.approx(sp.k0(Z), rel=1e-12) and abs(h.imag) < 1e-12
+    # theta = 0 gives Z = 0 and S -> infinity, so f -> 0 is not the parallel
+    # limit (the formula holds at large angles only); at theta = pi/2 it is
+    # bounded by 1
+    f = o.jaffe_angle(0.115, 2e-3, 2000.0, math.pi / 2, 1.73, 0.0356, ALPHA)
+    assert 0 < f < 1
+
+
+@pytest.mark.parametrize("u,f", [(0.5, 0.81093), (1.0, 0.69315), (2.0, 0.54931), (5.0, 0.35835)])
+def test_boag_2vm_values(u, f):
+    assert o.boag_2vm(u) == pytest.approx(f, abs=5e-6)
+
+
+def test_dt_rule_sits_on_the_von_neumann_bound():
+    # Eq. (vNeum): 2(sx+sy+sz) + cz^2 = 1 for the limiting species at dt_vN
+    dx, V, d = 2e-4, 200.0, 0.02
+    dt = o.dt_von_neumann(dx, V, d, MU, DD)
+    E = V / d
+    vals = [6 * D * dt / dx ** 2 + (m * E * dt / dx) ** 2 for m, D in zip(MU, DD)]
+    assert max(vals) == pytest.approx(1.0, rel=1e-12)
+    assert all(v <= 1.0 + 1e-12 for v in vals)
+    dtu = o.dt_von_neumann(dx, V, d, MU, DD, scheme=o.SCHEME_UPWIND)
+    vals = [6 * D * dtu / dx ** 2 + (m * E * dtu / dx) for m, D in zip(MU, DD)]
+    assert max(vals) == pytest.approx(1.0, rel=1e-12)
+    # reaction bound alpha dt n_peak = kappa
+    npk = o.peak_track_density([1000.0], [1e-3])
+    assert npk == pytest.approx(1000.0 * 1e7 / 34.0 / (math.pi * 1e-6), rel=1e-14)
+    dtr = o.dt_rule(5e-4, 50.0, 0.2, MU, DD, ALPHA, n_peak=npk, kappa=0.5)
+    assert ALPHA * dtr * npk == pytest.approx(0.5, rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# deposition (Eqs. linear_density, Gaussian, created, unity)
+# --------------------------------------------------------------------------
+
+def test_deposit_periodic_releases_N0_times_gap():
+    # Eq. (created): N_released = N0 * l exactly when nothing is clipped
+    O = o.Oracle(24, 20, 7, 5e-4, 1e-9, lateral_bc=o.LATERAL_PERIODIC)
+    tr = synth.uniform_tracks(3, 11, 24 * 5e-4, 20 * 5e-4, 1e-3)
+    rel = O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+    want = float(np.sum(tr.let_keV_um * 1e7 / 34.0)) * 7 * 5e-4
+    assert rel == pytest.approx(want, rel=1e-12)
+    t = O.tallies()
+    assert t.in_domain[0] == pytest.approx(want, rel=1e-12)
+    assert np.array_equal(O.density(0), O.density(1))
+    # z-independent: every plane is identical
+    n = O.density(0)
+    assert np.array_equal(n[0], n[6])
+
+
+def test_deposit_absorbing_clips_the_gaussian_tail():
+    # a track a distance a from one face loses erfc(a/b)/2 of its charge
+    # (a 1D Gaussian of density exp(-x^2/b^2)/(sqrt(pi) b)): b is not sigma
+    dx, b = 2e-4, 1e-3
+    nx = 60
+    a = 3.3e-4
+    O = o.Oracle(nx, nx, 3, dx, 1e-9, lateral_bc=o.LATERAL_ABSORBING)
+    rel = O.deposit([a], [nx * dx / 2], [1.0], [b])
+    full = 1.0 * 1e7 / 34.0 * 3 * dx
+    want = full * (1.0 - 0.5 * math.erfc(a / b))
+    assert rel == pytest.approx(want, rel=1e-10)
+
+
+def test_deposit_cell_density_matches_point_gaussian_at_fine_grid():
+    # Eq. (Gaussian) n0(r) = N0/(pi b^2) exp(-r^2/b^2) sampled at cell centres,
+    # and Eq. (unity): Simpson's rule over the plane gives I0 = N0.
+    b, dx, nx = 1e-3, 5e-5, 200        # dx = b/20, Lx = 10 b (Fig. 2 grid rule)
+    O = o.Oracle(nx, nx, 1, dx, 1e-12, lateral_bc=o.LATERAL_ABSORBING)
+    xc = yc = nx * dx / 2 + 0.3 * dx
+    O.deposit([xc], [yc], [0.115], [b])
+    plane = O.density(0)[0]
+    N0 = 0.115 * 1e7 / 34.0
+    xs = (np.arange(nx) + 0.5) * dx
+    X, Y = np.meshgrid(xs, xs)
+    point = N0 / (math.pi * b * b) * np.exp(-((X - xc) ** 2 + (Y - yc) ** 2) / b ** 2)
+    assert np.max(np.abs(plane - point)) / point.max() < 2e-3
+    I0 = integrate.simpson(integrate.simpson(point, x=xs, axis=1), x=xs)
+    assert I0 / N0 == pytest.approx(1.0, abs=1e-6)
+    # cell averages conserve exactly the mass inside the box: the product of
+    # the 1D Gaussian masses between the faces (a tail of ~erfc(5) is outside)
+    L = nx * dx
+    inside = (0.5 * (math.erf((L - xc) / b) + math.erf(xc / b))) ** 2
+    assert plane.sum() * dx * dx / N0 == pytest.approx(inside, rel=1e-13)
+    assert 1.0 - inside > 1e-12
+
+
+# --------------------------------------------------------------------------
+# transport invariants (Appendix scheme)
+# --------------------------------------------------------------------------
+
+def _plane_variance(m, dx):
+    ny, nx = m.shape
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dx
+    w = m / m.sum()
+    mx = np.sum(w * x[None, :]); my = np.sum(w * y[:, None])
+    vx = np.sum(w * (x[None, :] - mx) ** 2); vy = np.sum(w * (y[:, None] - my) ** 2)
+    return vx, vy
+
+
+def test_pure_diffusion_variance_grows_2Ddt_per_step_and_follows_closed_form():
+    # FTCS is a lattice random walk: on a plane whose z-neighbours hold the
+    # same values (the mid-plane of a z-uniform track, before the electrodes
+    # are felt there: one cell per step) each lateral variance grows by
+    # exactly 2 D dt per step; the profile follows Eq. (Gaussian) with
+    # b^2 -> b^2 + 4 D t.
+    b, dx, nx, nz = 1e-3, 2e-4, 60, 90
+    D = (0.037, 0.05)
+    dt = 2e-9
+    steps = 40
+    O = o.Oracle(nx, nx, nz, dx, dt, mu=(0, 0), D=D, alpha=0.0, voltage_V=0.0,
+                 lateral_bc=o.LATERAL_PERIODIC)
+    c = nx * dx / 2
+    O.deposit([c], [c], [1.0], [b])
+    v0 = [_plane_variance(O.density(s)[nz // 2], dx) for s in range(2)]
+    O.step(steps)
+    for s in range(2):
+        vx, vy = _plane_variance(O.density(s)[nz // 2], dx)
+        inc = 2 * D[s] * dt * steps
+        assert vx - v0[s][0] == pytest.approx(inc, rel=1e-9)
+        assert vy - v0[s][1] == pytest.approx(inc, rel=1e-9)
+    # shape against the closed form (mid-plane, normalised)
+    n = O.density(0)[nz // 2]
+    xs = (np.arange(nx) + 0.5) * dx
+    X, Y = np.meshgrid(xs, xs)
+    ref = o.gaussian_track_diffused(np.hypot(X - c, Y - c), dt * steps, 1.0, b, D[0])
+    err = np.max(np.abs(n / n.sum() - ref / ref.sum())) / np.max(ref / ref.sum())
+    assert err < 1e-2
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_z_sine_mode_is_an_eigenvector_with_dirichlet_electrodes(m):
+    # n_k = sin(pi m (k+1)/(nz+1)) with n = 0 at k = -1 and k = nz decays by
+    # 1 - 4 s_z sin^2(pi m / (2(nz+1))) per step (3-point Laplacian)
+    nz, dx, dt, D = 30, 1e-3, 5e-9, 0.04
+    O = o.Oracle(4, 4, nz, dx, dt, mu=(0, 0), D=(D, D), alpha=0.0, voltage_V=0.0)
+    k = np.arange(nz)
+    prof = np.sin(math.pi * m * (k + 1) / (nz + 1))
+    field = np.broadcast_to(prof[:, None, None], (nz, 4, 4)) * 1e9
+    O.set_density(field, field)
+    steps = 25
+    O.step(steps)
+    s = D * dt / dx ** 2
+    lam = 1.0 - 4.0 * s * math.sin(math.pi * m / (2 * (nz + 1))) ** 2
+    got = O.density(0)[:, 1, 2]
+    np.testing.assert_allclose(got, prof * 1e9 * lam ** steps, rtol=1e-12, atol=1e-12 * 1e9)
+    t = O.tallies()
+    assert t.released[0] == pytest.approx(t.in_domain[0] + t.collected[0], rel=1e-13)
+
+
+def _z_blob(nz, k0, w):
+    k = np.arange(nz)
+    return np.exp(-((k - k0) / w) ** 2)
+
+
+@pytest.mark.parametrize("scheme", [o.SCHEME_LAX_WENDROFF, o.SCHEME_UPWIND])
+def test_drift_moments(scheme):
+    # Lax-Wendroff: centroid moves c dx per step, variance grows 2 s_z dx^2.
+    # Upwind: centroid c dx, variance 2 s_z dx^2 + c (1 - c) dx^2.
+    # Positive ions move to +z, negative ions to -z.
+    nz, dx, V = 200, 1e-3, 40.0
+    D = (0.02, 0.03)
+    mu = (1.36, 2.10)
+    dt = 0.5 * o.dt_von_neumann(dx, V, nz * dx, mu, D, scheme)
+    O = o.Oracle(2, 2, nz, dx, dt, mu=mu, D=D, alpha=0.0, voltage_V=V, scheme=scheme)
+    blob = _z_blob(nz, 100.0, 6.0)
+    f = np.broadcast_to(blob[:, None, None], (nz, 2, 2))
+    O.set_density(f, f)
+    def moments(s):
+        p = O.density(s)[:, 0, 0]
+        k = np.arange(nz)
+        w = p / p.sum()
+        m = np.sum(w * k)
+        return m, np.sum(w * (k - m) ** 2)
+    m0 = [moments(s) for s in range(2)]
+    steps = 30
+    O.step(steps)
+    E = V / (nz * dx)
+    for s, sign in ((0, 1.0), (1, -1.0)):
+        c = mu[s] * E * dt / dx
+        sz = D[s] * dt / dx ** 2
+        m1, v1 = moments(s)
+        assert m1 - m0[s][0] == pytest.approx(sign * c * steps, rel=1e-9)
+        dv = 2 * sz + (c * (1 - c) if scheme == o.SCHEME_UPWIND else 0.0)
+        assert v1 - m0[s][1] == pytest.approx(dv * steps, rel=1e-8)
+
+
+def test_lax_wendroff_at_c_equal_one_is_an_exact_shift():
+    # c = 1, s = 0: every carrier moves exactly one cell per step.  All
+    # quantities are powers of two so that c is exactly 1.
+    nz = 16
+    dx = 2.0 ** -10
+    O = o.Oracle(1, 1, nz, dx, dx, mu=(1.0, 1.0), D=(0.0, 0.0), alpha=0.0,
+                 voltage_V=nz * dx)
+    p = np.zeros((nz, 1, 1)); p[3, 0, 0] = 5.0; p[4, 0, 0] = 7.0
+    O.set_density(p, p)
+    O.step(2)
+    a = O.density(0)[:, 0, 0]; bneg = O.density(1)[:, 0, 0]
+    want_p = np.zeros(nz); want_p[5] = 5.0; want_p[6] = 7.0
+    want_m = np.zeros(nz); want_m[1] = 5.0; want_m[2] = 7.0
+    assert np.array_equal(a, want_p) and np.array_equal(bneg, want_m)
+    O.step(1)       # n- now at cells 0, 1 (5 and 7): nothing has reached the anode
+    t = O.tallies()
+    assert t.collected_anode[1] == 0.0
+    O.step(1)
+    t = O.tallies()
+    assert t.collected_anode[1] == 5.0 * dx ** 3
+    O.step(1)
+    t = O.tallies()
+    assert t.collected_anode[1] == 12.0 * dx ** 3 and t.collected_cathode[1] == 0.0
+    assert t.in_domain[1] == 0.0
+
+
+@pytest.mark.parametrize("bc", [o.LATERAL_PERIODIC, o.LATERAL_ABSORBING])
+def test_charge_conservation_with_and_without_recombination(bc):
+    # released = in domain + collected + lost laterally + recombined, every
+    # step; the collected charge comes from the electrode ghost cells, not
+    # from the sums, so this is not an identity of the bookkeeping.
+    nx, nz, dx = 20, 30, 5e-4
+    for alpha in (0.0, ALPHA):
+        tr = synth.uniform_tracks(11, 9, nx * dx, nx * dx, 1.5e-3, let=("mixture", [(50.0, 1.0)]))
+        dt = o.dt_rule(dx, 100.0, nz * dx, MU, DD, alpha, n_peak=o.peak_track_density(tr.let_keV_um, tr.b_cm))
+        O = o.Oracle(nx, nx, nz, dx, dt, alpha=alpha, voltage_V=100.0, lateral_bc=bc)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        for _ in range(6):
+            O.step(7)
+            t = O.tallies()
+            for s in range(2):
+                total = t.in_domain[s] + t.collected[s] + t.lost_lateral[s] + t.recombined
+                assert total == pytest.approx(t.released[s], rel=1e-12)
+        if alpha == 0.0:
+            assert t.recombined == 0.0
+        if bc == o.LATERAL_PERIODIC:
+            assert np.all(t.lost_lateral == 0.0)
+
+
+def test_recombination_recurrence_and_continuum_limit():
+    # E = 0, D = 0, uniform n+ = n- = n0: n <- n - alpha dt n^2 exactly, and
+    # n(t) -> n0/(1 + alpha n0 t) as dt -> 0 with error O(alpha n0 dt)
+    n0, T = 4e12, 2e-6
+    errs = []
+    for nsteps in (50, 100, 200):
+        dt = T / nsteps
+        O = o.Oracle(3, 3, 4, 1e-3, dt, mu=(0, 0), D=(0, 0), alpha=ALPHA, voltage_V=0.0)
+        f = np.full((4, 3, 3), n0)
+        O.set_density(f, f)
+        O.step(nsteps)
+        n = n0
+        for _ in range(nsteps):
+            n = n - ALPHA * dt * n * n
+        got = O.density(0)
+        assert np.all(got == got[0, 0, 0]) and np.array_equal(got, O.density(1))
+        assert got[0, 0, 0] == pytest.approx(n, rel=1e-14)
+        errs.append(abs(got[0, 0, 0] - n0 / (1 + ALPHA * n0 * T)))
+    assert errs[1] < 0.55 * errs[0] and errs[2] < 0.55 * errs[1]   # first order in dt
+
+
+def test_mirror_symmetry_is_bitwise():
+    # mu+ = mu-, D+ = D-: n+(i,j,k) = n-(i,j,nz-1-k) at every step; anode and
+    # cathode collections swap.  Catches a wrong upwind side or drift sign.
+    nx, nz, dx = 16, 24, 5e-4
+    tr = synth.uniform_tracks(5, 6, nx * dx, nx * dx, 1e-3)
+    dt = o.dt_rule(dx, 150.0, nz * dx, (1.8, 1.8), (0.04, 0.04), ALPHA,
+                   n_peak=o.peak_track_density(tr.let_keV_um, tr.b_cm))
+    O = o.Oracle(nx, nx, nz, dx, dt, mu=(1.8, 1.8), D=(0.04, 0.04), alpha=ALPHA,
+                 voltage_V=150.0, lateral_bc=o.LATERAL_ABSORBING)
+    O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+    for _ in range(4):
+        O.step(5)
+        assert np.array_equal(O.density(0), O.density(1)[::-1])
+    t = O.tallies()
+    assert t.collected_anode[0] == t.collected_cathode[1]
+    assert t.collected_cathode[0] == t.collected_anode[1]
+
+
+# --------------------------------------------------------------------------
+# physics pins: Jaffe (initial recombination) and Boag (general recombination)
+# --------------------------------------------------------------------------
+
+def _single_track_f(let, b=1e-3, dx=2e-4, V=200.0, gap=0.02, mu=MU, D=DD, tol=1e-9):
+    nz = int(round(gap / dx)); nxy = int(round(9.6 * b / dx))
+    dt = o.dt_rule(dx, V, gap, mu, D, ALPHA, n_peak=o.peak_track_density([let], [b]))
+    O = o.Oracle(nxy, nxy, nz, dx, dt, mu=mu, D=D, alpha=ALPHA, voltage_V=V,
+                 lateral_bc=o.LATERAL_ABSORBING)
+    c = 0.5 * nxy * dx
+    O.deposit([c], [c], [let], [b])
+    for _ in range(400):
+        O.step(25)
+        t = O.tallies()
+        if t.in_domain.sum() / t.released.sum() < tol:
+            break
+    return t
+
+
+@pytest.mark.parametrize("let,tol", [(0.1, 1e-4), (1.0, 5e-4), (3.0, 2e-3)])
+def test_single_track_matches_jaffe_where_its_gaussian_ansatz_holds(let, tol):
+    # Eq. (Jaffe_noangle) with mean mu and D (reading of the text beside it)
+    # for a track parallel to E; 48x48x100 cells at dx = b/5, 200 V over 200 um.
+    t = _single_track_f(let)
+    fj = o.jaffe_parallel(let, 1e-3, 0.02, 1e4, 0.5 * sum(MU), 0.5 * sum(DD), ALPHA)
+    assert abs(t.f - fj) < tol
+
+
+@pytest.mark.slow
+def test_single_track_jaffe_gap_shrinks_with_dx():
+    # Sec. Stability and accuracy (ii): f converges as dx decreases
+    fj = o.jaffe_parallel(1.0, 1e-3, 0.02, 1e4, 1.80, 0.037, ALPHA)
+    e5 = abs(_single_track_f(1.0, dx=2e-4).f - fj)
+    e10 = abs(_single_track_f(1.0, dx=1e-4).f - fj)
+    assert e10 < 0.3 * e5 and e10 < 5e-5
+
+
+def test_proton_initial_recombination_below_0p1_percent():
+    # Table 1 proton (LET 7.76e-4 keV/um, b = 10 um): 1 - f < 1e-3
+    g = _gold("paper_tables.json")
+    p = g["table1_track_parameters"]["proton"]
+    t = _single_track_f(p["LET_keV_um"], b=p["b_um"] * 1e-4)
+    assert 0.0 <= 1.0 - t.f < g["proton_initial_recombination_bound"]["one_minus_f_max"]
+
+
+@pytest.mark.parametrize("u", [0.5, 1.0, 2.0, 5.0])
+def test_uniform_slab_follows_boag_two_voltage_method(u):
+    # A laterally uniform slab n over the whole gap released by one pulse:
+    # f = ln(1+u)/u, u = alpha/(mu+ + mu-) n d^2 / V.  The diffusion
+    # broadening of the fronts is the expected residual.
+    nz, dx, V = 400, 5e-4, 200.0
+    d = nz * dx
+    n = u * (MU[0] + MU[1]) * V / (ALPHA * d * d)
+    dt = o.dt_rule(dx, V, d, MU, DD, ALPHA, n_peak=n)
+    O = o.Oracle(4, 4, nz, dx, dt, alpha=ALPHA, voltage_V=V)
+    f = np.full((nz, 4, 4), n)
+    O.set_density(f, f)
+    while True:
+        O.step(200)
+        t = O.tallies()
+        if t.in_domain.sum() / t.released.sum() < 1e-9:
+            break
+    assert t.f == pytest.approx(o.boag_2vm(u), abs=1e-2)
