@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the IonTracks transport step on GB300.
+
+Workload: the pulsed-beam grid, 256 x 256 x 400 cells at dx = 5 um (2 mm
+gap), FP32 densities with FP64 tallies, periodic lateral faces, 2000 tracks
+per pulse at seeded uniform (x, y) with log-uniform LET 1-1000 keV/um and
+b = 10 um, 200 V.  One benchmark step is one pulse period: the pulse is
+deposited and then ``--seg`` explicit time steps (default 200) are taken.
+Metric: Gcell-updates/s (cells x time steps / s).
+
+  value  -- device-timed (CUDA events on the library's stream), tracks resident in HBM
+  e2e    -- through the public C API with host buffers: pinned track upload,
+            deposit, steps, tally read-back, on the host clock
+  roofline -- the step kernel: 16 algorithmic bytes per FP32 cell-update
+            (read and write n+ and n-) / its average duration, against the
+            measured HBM copy bandwidth
+  cpu_baseline -- the FP64 CPU oracle on the host cores, bounded sample
+
+``--impl reference`` times the oracle (the reference arm of this project) on
+the same workload.  Under torchrun every rank runs an independent replica
+(weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL_UPDATE = 16          # FP32: read n+, n- once, write them once
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "step_zmarch_pulsed_256x256x400.json")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in mp:
+                v = mp[key]
+                v = v.get("value", v) if isinstance(v, dict) else v
+                return float(v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for name in ("it_zmarch.cu", "it_device.cuh", "it_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1610_06749_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when the kernel source has changed since it was captured."""
+    try:
+        with open(PROFILE) as f:
+            prof = json.load(f)
+        if prof.get("kernel_sha") == kernel_sha():
+            return float(prof["dram_bytes_per_launch_full_size"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.tmp:
+            return None
+        try:
+            rows = [r.split(",") for r in open(self.tmp.name).read().strip().splitlines() if r.strip()]
+            os.unlink(self.tmp.name)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(w, tracks, seconds):
+    """Oracle Gcell-updates/s on the host cores, bounded sample of the workload."""
+    import oracle.oracle as o
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    dt = o.dt_rule(w.dx_cm, w.voltage_V, w.gap_cm, n_peak=o.peak_track_density(tracks.let_keV_um, tracks.b_cm))
+    O = o.Oracle(w.nx, w.ny, w.nz, w.dx_cm, dt, voltage_V=w.voltage_V)
+    O.deposit(tracks.x_cm, tracks.y_cm, tracks.let_keV_um, tracks.b_cm)
+    t0 = time.perf_counter()
+    O.step(1)
+    one = time.perf_counter() - t0
+    n = max(1, int(seconds / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    O.step(n)
+    el = time.perf_counter() - t0
+    O.close()
+    return w.cells * n / el / 1e9, int(os.environ.get("OMP_NUM_THREADS", cores)), n, el
+
+
+def run_reference(args, ws, rank):
+    from paper_1610_06749_gb300 import synth
+    import oracle.oracle as o
+    if rank != 0:
+        return
+    w = synth.pulsed_256x256x400(args.voltage)
+    tracks = synth.pulsed_tracks(w)
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    dt = o.dt_rule(w.dx_cm, w.voltage_V, w.gap_cm, n_peak=o.peak_track_density(tracks.let_keV_um, tracks.b_cm))
+    O = o.Oracle(w.nx, w.ny, w.nz, w.dx_cm, dt, voltage_V=w.voltage_V)
+    O.deposit(tracks.x_cm, tracks.y_cm, tracks.let_keV_um, tracks.b_cm)
+    for _ in range(args.warmup):
+        O.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(1)
+    el = time.perf_counter() - t0
+    val = w.cells * args.steps / el / 1e9
+    sample = (f"FP64 oracle, {args.steps} explicit steps of the {w.nx}x{w.ny}x{w.nz} pulsed grid after one "
+              f"2000-track pulse (one oracle step per benchmark step)")
+    line = {"impl": "reference", "metric": "Gcell-updates/s", "value": val, "unit": "Gcell-updates/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "cells": w.cells, "tracks_per_pulse": 2000},
+            "cpu_baseline": {"value": val, "unit": "Gcell-updates/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1610_06749_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1610_06749_gb300 import binding as B
+    from paper_1610_06749_gb300 import synth
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = synth.pulsed_256x256x400(args.voltage)
+    w.seed += 7919 * rank                          # independent replica per rank
+    tracks = synth.pulsed_tracks(w)
+    ntr = len(tracks)
+    npk = B.it_peak_density(tracks.let_keV_um, tracks.b_cm)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        sim = B.Simulation(w.nx, w.ny, w.nz, w.dx_cm, w.voltage_V, n_peak_cm3=npk, torch_state=True)
+    launch = sim.launch()
+    packed = np.stack([tracks.x_cm, tracks.y_cm, tracks.let_keV_um, tracks.b_cm], axis=1)
+    d_tracks = torch.from_numpy(np.ascontiguousarray(packed)).to(dev)
+    xy_host = np.ascontiguousarray(np.stack([tracks.x_cm, tracks.y_cm], axis=1))
+    cells, seg = w.cells, args.seg
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def maxover(x):
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([x], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    def dev_step():
+        B.it_deposit_tracks_device(sim.h, ntr, d_tracks.data_ptr())
+        sim.step(seg)
+
+    # ---- device-timed throughput (inputs resident in HBM) ----
+    for _ in range(args.warmup):
+        dev_step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            dev_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    t_dev = maxover(ev0.elapsed_time(ev1) / 1e3)
+    clocks = clk.summary()
+
+    # ---- step-kernel duration (graph replays, no deposits), same stream ----
+    nk = max(2 * seg, 1000)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sim.step(64)
+    torch.cuda.synchronize()
+    k0.record(stream)
+    sim.step(nk)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    t_kernel = k0.elapsed_time(k1) / 1e3 / nk
+
+    # ---- end to end through the public API with host buffers ----
+    def e2e_step():
+        B.it_deposit_tracks(sim.h, xy_host, tracks.let_keV_um, tracks.b_cm)   # pinned staging H2D
+        sim.step(seg)
+        return sim.tallies()                                                    # D2H of the tallies
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        t = e2e_step()
+    t_e2e = maxover(time.perf_counter() - t0)
+    barrier()
+
+    total_updates = cells * seg * args.steps * ws
+    value = total_updates / t_dev / 1e9
+    e2e_value = total_updates / t_e2e / 1e9
+    peak, peak_kind = hbm_peak()
+    achieved = BYTES_PER_CELL_UPDATE * cells / t_kernel / 1e9
+    traffic = ncu_traffic()
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            rate, cores, n, el = cpu_oracle_rate(w, tracks, args.cpu_seconds)
+            cpu = {"value": rate, "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+                   "sample": f"FP64 oracle, {n} explicit steps of the {w.nx}x{w.ny}x{w.nz} pulsed grid after "
+                             f"one 2000-track pulse ({el:.1f} s)"}
+        line = {
+            "metric": "Gcell-updates/s", "value": value, "unit": "Gcell-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "dx_um": w.dx_cm * 1e4,
+                       "tracks_per_pulse": ntr, "time_steps_per_step": seg, "voltage_V": w.voltage_V,
+                       "tallies": "f64", "kernel": "zmarch" if launch["kernel"] == B.IT_KERNEL_ZMARCH else "simple",
+                       "launch": launch, "l2": "inputs larger than L2 (210 MB state read per time step)",
+                       "parallelism": f"replicas{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "step_zmarch_kernel", "kernel_us": t_kernel * 1e6,
+                         "bytes_per_launch": BYTES_PER_CELL_UPDATE * cells},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": ntr * 4 * 8,
+                    "d2h_bytes_per_step": 17 * 8},
+            "gpu_launches": args.steps * (seg + 4),
+            "clocks": clocks,
+            "f_last": t.f,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30, help="benchmark steps (pulse periods) timed")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seg", type=int, default=200, help="explicit time steps per benchmark step")
+    ap.add_argument("--voltage", type=float, default=200.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * iontracks.h -- C ABI of the GB300 IonTracks transport library.
+ *
+ * The library evolves the positive and negative charge-carrier densities n+
+ * and n- of an ionization chamber between two parallel electrodes
+ * (Christensen, Toelli, Bassler, arXiv:1610.06749, Sec. "Charge carrier
+ * movements", Eq. theEquation without the space-charge term):
+ *
+ *   dn+/dt = D+ lap n+ - mu+ E dn+/dz - alpha n+ n-
+ *   dn-/dt = D- lap n- + mu- E dn-/dz - alpha n+ n-
+ *
+ * with the explicit scheme of the Appendix (forward Euler in time, the
+ * blended backward/central drift derivative, which is Lax-Wendroff, and the
+ * 3-point Laplacian), the time step bounded by Eq. (vNeum), Dirichlet
+ * electrodes (Sec. Methods), Gaussian track deposition (Eqs. linear_density,
+ * Gaussian, created) and tallies of released, recombined and collected
+ * charge that give f = N_collected / N_released (Eq. collection_efficiency).
+ *
+ * Conventions (every entry point):
+ *   - Units are CGS: cm, s, V, ions/cm^3; LET in keV/um; W in eV.
+ *   - Return 0 (IT_OK) on success or a negative IT_E* code; nothing throws or
+ *     aborts across the ABI.  it_last_error() gives a message for the last
+ *     failure on the calling thread.
+ *   - Host arrays passed in are read before the call returns; the caller
+ *     keeps ownership.  Device memory the library allocates is freed by
+ *     it_destroy; memory handed in through it_create_ex is never freed.
+ *   - Work is enqueued on the context's CUDA stream; calls that return host
+ *     results (it_tallies, it_get_density) synchronise that stream.
+ *   - Grid layout of a density field: [nz][ny][nx], x fastest, densities of
+ *     cell (i,j,k) whose extent is [i dx,(i+1) dx) x [j dx,(j+1) dx) x
+ *     [k dx,(k+1) dx); the anode is the face z = 0, the cathode z = nz dx.
+ *   - The library holds no CPU fallback: without a CUDA device every call
+ *     that needs one returns IT_ECUDA.
+ */
+#ifndef IONTRACKS_H
+#define IONTRACKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define IT_OK        0
+#define IT_EINVAL   -1   /* bad argument or inconsistent parameters */
+#define IT_ENOMEM   -2   /* device or host allocation failed */
+#define IT_ECUDA    -3   /* a CUDA call failed (message in it_last_error) */
+#define IT_EUNSTABLE -4  /* dt violates Eq. (vNeum) or the state went non-finite */
+#define IT_ETIMEOUT -5   /* a bounded wait ran out */
+#define IT_ESTATE   -6   /* call not valid in the context's current state */
+
+/* it_params.precision: storage and update type of the densities; tallies are
+ * always accumulated in FP64 */
+#define IT_FP32 0
+#define IT_FP64 1
+/* it_params.lateral_bc: x/y faces.  The paper only asks that Lx, Ly be large
+ * enough (Sec. Methods); periodic faces stand for a uniformly irradiated
+ * chamber (Sec. Distribution of ion tracks), absorbing faces count what
+ * leaves them in lost_lateral. */
+#define IT_PERIODIC  0
+#define IT_ABSORBING 1
+/* it_params.scheme: drift derivative.  IT_LAX_WENDROFF is the Appendix's
+ * blended derivative; IT_UPWIND the pure backward (upwind) difference. */
+#define IT_LAX_WENDROFF 0
+#define IT_UPWIND       1
+/* it_params.kernel: which step kernel runs (both are CUDA). */
+#define IT_KERNEL_AUTO   0   /* z-march kernel where the grid allows, else simple */
+#define IT_KERNEL_SIMPLE 1   /* one thread per cell, global loads */
+#define IT_KERNEL_ZMARCH 2   /* TMA-staged z-planes in shared memory (FP32, nx % 4 == 0) */
+
+typedef struct it_ctx it_ctx;
+
+typedef struct {
+    int32_t nx, ny, nz;     /* cells; gap = nz * dx */
+} it_grid;
+
+typedef struct {
+    double mu[2];           /* mobilities [0] = positive, [1] = negative ions, cm^2/(V s) */
+    double D[2];            /* diffusion constants, cm^2/s */
+    double alpha;           /* recombination constant, cm^3/s */
+    double W_eV;            /* mean energy per ion pair, eV (Eq. linear_density) */
+    double gap_cm;          /* electrode gap d; must equal nz * dx (rel. 1e-9) */
+    double voltage_V;       /* polarisation voltage; E = V / d along +z */
+    int32_t precision;      /* IT_FP32 | IT_FP64 */
+    int32_t lateral_bc;     /* IT_PERIODIC | IT_ABSORBING */
+    int32_t scheme;         /* IT_LAX_WENDROFF | IT_UPWIND */
+    int32_t kernel;         /* IT_KERNEL_* */
+    double cfl_safety;      /* automatic dt = cfl_safety * dt_vN (default 1) */
+    double react_kappa;     /* automatic dt <= react_kappa / (alpha n_peak) (default 0.5) */
+    double n_peak_cm3;      /* peak density for that bound; 0 disables it */
+} it_params;
+
+typedef struct {
+    double released[2];          /* ions released per species (deposited in the domain) */
+    double collected_anode[2];   /* ions that left through z = 0 (signed) */
+    double collected_cathode[2]; /* ions that left through z = d (signed) */
+    double lost_lateral[2];      /* ions that left through absorbing x/y faces */
+    double in_domain[2];         /* ions still in the domain */
+    double recombined;           /* ion pairs recombined */
+    double f;                    /* (collected+ + collected-) / (released+ + released-) */
+    double t_s;                  /* simulated time */
+    double dt_s;                 /* time step */
+    int64_t steps;               /* steps taken */
+    double n_min[2], n_max[2];   /* extreme densities of the current state */
+} it_tallies_t;
+
+/* Library version string (static storage). */
+const char *it_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *it_last_error(void);
+
+/* Fill *p with the defaults: mu = 1.73 / 1.87, D = 0.037 / 0.037,
+ * alpha = 1.6e-6, W = 34 eV, gap 0 (must be set), 0 V, FP32, periodic,
+ * Lax-Wendroff, automatic kernel, cfl_safety 1, react_kappa 0.5, n_peak 0.
+ * Returns IT_EINVAL if p is NULL. */
+int it_params_default(it_params *p);
+
+/* Largest time step allowed by Eq. (vNeum) for both species with E along z:
+ * 2(sx+sy+sz) + cz^2 <= 1 (Lax-Wendroff) or 2(sx+sy+sz) + cz <= 1 (upwind),
+ * s = D dt/dx^2, c = mu E dt/dx, times p->cfl_safety, and, when
+ * p->n_peak_cm3 > 0 and alpha > 0, no larger than react_kappa/(alpha n_peak)
+ * (the paper gives no bound for the reaction term; this keeps the explicit
+ * recombination step monotone).  Writes the result to *dt_out. */
+int it_auto_dt(const it_params *p, double dx_cm, double *dt_out);
+
+/* Largest central density N0/(pi b^2), N0 = LET/W (Eqs. linear_density,
+ * Gaussian) over n tracks; host arrays of n doubles.  For it_params.n_peak_cm3. */
+int it_peak_density(int64_t n, const double *let_keV_um, const double *b_cm,
+                    double W_eV, double *n_peak_out);
+
+/* Bytes of device state a context of this grid and precision needs when the
+ * caller provides it (it_create_ex): two ping-pong sets of both species. */
+int it_state_bytes(it_grid g, int32_t precision, size_t *bytes_out);
+
+/* Create a simulation with library-owned device memory on the current CUDA
+ * device and a library-owned non-blocking stream.  dt_s <= 0 selects
+ * it_auto_dt.  Densities start at zero.  Errors: IT_EINVAL (grid < 1 cell,
+ * dx or constants non-positive or NaN, |gap - nz dx| > 1e-9 gap, dt above
+ * the Eq. (vNeum) bound), IT_ENOMEM, IT_ECUDA. */
+int it_create(it_grid g, double dx_cm, double dt_s, const it_params *p, it_ctx **out);
+
+/* As it_create, but the density state lives in caller-owned device memory
+ * dev_state of at least it_state_bytes() bytes (256-byte aligned), and work
+ * is enqueued on the caller's stream (a cudaStream_t; NULL = a library
+ * stream).  The library never frees dev_state or the stream. */
+int it_create_ex(it_grid g, double dx_cm, double dt_s, const it_params *p,
+                 void *dev_state, size_t bytes, void *stream, it_ctx **out);
+
+/* Deposit n tracks parallel to the field now (instantaneous ionisation,
+ * Sec. Implementation).  xy_cm: 2n doubles (x0,y0,x1,y1,...), let_keV_um and
+ * b_cm: n doubles each, all host memory.  Each cell gains N0 wx wy / dx^2 on
+ * every z plane for both species, wx = (erf((x_{i+1}-xc)/b) -
+ * erf((x_i-xc)/b))/2 over a window of +-ceil(6 b/dx) cells around the centre
+ * cell (wrapped when periodic, clipped when absorbing); released grows by what
+ * landed in the domain.  n = 0 is a no-op.  Errors: IT_EINVAL for NULL arrays
+ * with n > 0, b <= 0, LET < 0 or a non-finite value. */
+int it_deposit_tracks(it_ctx *ctx, int64_t n, const double *xy_cm,
+                      const double *let_keV_um, const double *b_cm);
+
+/* As it_deposit_tracks, but the tracks are already in device memory as
+ * n x 4 doubles (x_cm, y_cm, LET_keV_um, b_cm per track, 16-byte aligned),
+ * enqueued on the context stream; nothing is validated on the host, so
+ * values must be finite with b > 0.  For inputs kept resident in HBM. */
+int it_deposit_tracks_device(it_ctx *ctx, int64_t n, const double *dev_tracks);
+
+/* Schedule n tracks to be deposited at the start of step step_idx[i]
+ * (counted from the context's step 0; Poisson-timed arrivals of a continuous
+ * beam, Sec. Distribution of ion tracks).  Steps already taken are rejected
+ * with IT_EINVAL.  Arrays as in it_deposit_tracks plus n int64 step indices.
+ * Replaces any earlier schedule. */
+int it_schedule_tracks(it_ctx *ctx, int64_t n, const double *xy_cm,
+                       const double *let_keV_um, const double *b_cm,
+                       const int64_t *step_idx);
+
+/* Advance n_steps explicit steps (scheduled tracks deposited first at their
+ * steps).  Asynchronous on the context stream; launches are replayed from a
+ * captured CUDA graph in segments.  n_steps < 0 is IT_EINVAL. */
+int it_step(it_ctx *ctx, int64_t n_steps);
+
+/* Step until (in_domain+ + in_domain-) / (released+ + released-) < tol
+ * ("dragged completely apart", Sec. Implementation), checked every
+ * check_every steps, or until max_steps more steps.  *steps_done (may be NULL)
+ * receives the steps taken.  Returns IT_EUNSTABLE if the state went
+ * non-finite, IT_ETIMEOUT if max_steps ran out first. */
+int it_run_to_completion(it_ctx *ctx, double tol, int64_t max_steps,
+                         int64_t check_every, int64_t *steps_done);
+
+/* Synchronise and return all tallies (FP64, reduced in a fixed order so that
+ * reruns are bitwise identical). */
+int it_tallies(it_ctx *ctx, it_tallies_t *out);
+
+/* Copy one species' densities (0 = n+, 1 = n-) to host memory, [nz][ny][nx]
+ * in the context's precision (bytes must equal cells * element size). */
+int it_get_density(it_ctx *ctx, int species, void *host_dst, size_t bytes);
+
+/* Replace both species' densities with host arrays (context precision,
+ * [nz][ny][nx]) as an initial condition: all tallies restart, released
+ * becomes the FP64 sum of what was set, the step counter returns to 0. */
+int it_set_density(it_ctx *ctx, const void *plus, const void *minus, size_t bytes);
+
+/* Device pointers of the current n+ and n- fields (valid until the next
+ * it_step) and the context's stream (a cudaStream_t). */
+int it_device_state(it_ctx *ctx, void **plus, void **minus, void **stream);
+
+/* Choose the step kernel and, for IT_KERNEL_ZMARCH, its launch shape: rows
+ * per tile (a divisor of ny), z chunks per column and ring depth (3..8);
+ * 0 leaves a value to the built-in rule.  Only before the first step
+ * (IT_ESTATE otherwise).  IT_EINVAL if the shape does not fit the grid. */
+int it_set_launch(it_ctx *ctx, int kernel, int tile_rows, int z_chunks, int stages);
+
+/* Report the kernel in use, its launch shape and its CTA count. */
+int it_get_launch(it_ctx *ctx, int *kernel, int *tile_rows, int *z_chunks, int *stages, int *ctas);
+
+/* Destroy a context; NULL is a no-op.  Synchronises the stream first. */
+int it_destroy(it_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IONTRACKS_H */

@@ -1,0 +1,344 @@
+"""ctypes binding of ``libiontracks.so`` (include/iontracks.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  The functions keep the C names (``it_create``, ``it_step``, ...)
+and raise ``ItError`` on a non-zero return code.  ``Simulation`` bundles a
+context with numpy/torch conveniences.  There is no CPU fallback: if the
+shared library is missing this module raises on import of the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiontracks.so")
+
+IT_OK, IT_EINVAL, IT_ENOMEM, IT_ECUDA, IT_EUNSTABLE, IT_ETIMEOUT, IT_ESTATE = 0, -1, -2, -3, -4, -5, -6
+IT_FP32, IT_FP64 = 0, 1
+IT_PERIODIC, IT_ABSORBING = 0, 1
+IT_LAX_WENDROFF, IT_UPWIND = 0, 1
+IT_KERNEL_AUTO, IT_KERNEL_SIMPLE, IT_KERNEL_ZMARCH = 0, 1, 2
+
+_ERRNAMES = {IT_EINVAL: "IT_EINVAL", IT_ENOMEM: "IT_ENOMEM", IT_ECUDA: "IT_ECUDA",
+             IT_EUNSTABLE: "IT_EUNSTABLE", IT_ETIMEOUT: "IT_ETIMEOUT", IT_ESTATE: "IT_ESTATE"}
+
+
+class ItError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class it_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class it_params(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double * 2), ("D", ctypes.c_double * 2), ("alpha", ctypes.c_double),
+                ("W_eV", ctypes.c_double), ("gap_cm", ctypes.c_double), ("voltage_V", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("lateral_bc", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("cfl_safety", ctypes.c_double), ("react_kappa", ctypes.c_double),
+                ("n_peak_cm3", ctypes.c_double)]
+
+
+class it_tallies_t(ctypes.Structure):
+    _fields_ = [("released", ctypes.c_double * 2), ("collected_anode", ctypes.c_double * 2),
+                ("collected_cathode", ctypes.c_double * 2), ("lost_lateral", ctypes.c_double * 2),
+                ("in_domain", ctypes.c_double * 2), ("recombined", ctypes.c_double), ("f", ctypes.c_double),
+                ("t_s", ctypes.c_double), ("dt_s", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("n_min", ctypes.c_double * 2), ("n_max", ctypes.c_double * 2)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "(the library has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, D, I, I64, SZ = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        DP = ctypes.POINTER(ctypes.c_double)
+        I64P = ctypes.POINTER(ctypes.c_int64)
+        IP = ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "it_version": (ctypes.c_char_p, []),
+            "it_last_error": (ctypes.c_char_p, []),
+            "it_params_default": (I, [ctypes.POINTER(it_params)]),
+            "it_auto_dt": (I, [ctypes.POINTER(it_params), D, DP]),
+            "it_peak_density": (I, [I64, DP, DP, D, DP]),
+            "it_state_bytes": (I, [it_grid, ctypes.c_int32, ctypes.POINTER(SZ)]),
+            "it_create": (I, [it_grid, D, D, ctypes.POINTER(it_params), ctypes.POINTER(P)]),
+            "it_create_ex": (I, [it_grid, D, D, ctypes.POINTER(it_params), P, SZ, P, ctypes.POINTER(P)]),
+            "it_deposit_tracks": (I, [P, I64, DP, DP, DP]),
+            "it_deposit_tracks_device": (I, [P, I64, P]),
+            "it_schedule_tracks": (I, [P, I64, DP, DP, DP, I64P]),
+            "it_step": (I, [P, I64]),
+            "it_run_to_completion": (I, [P, D, I64, I64, I64P]),
+            "it_tallies": (I, [P, ctypes.POINTER(it_tallies_t)]),
+            "it_get_density": (I, [P, I, P, SZ]),
+            "it_set_density": (I, [P, P, P, SZ]),
+            "it_device_state": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),
+            "it_set_launch": (I, [P, I, I, I, I]),
+            "it_get_launch": (I, [P, IP, IP, IP, IP, IP]),
+            "it_destroy": (I, [P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != IT_OK:
+        raise ItError(rc, lib().it_last_error().decode(errors="replace"))
+    return rc
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# thin wrappers with the C names
+# --------------------------------------------------------------------------
+
+def it_version() -> str:
+    return lib().it_version().decode()
+
+
+def it_last_error() -> str:
+    return lib().it_last_error().decode(errors="replace")
+
+
+def it_params_default(**kw) -> it_params:
+    p = it_params()
+    _check(lib().it_params_default(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k in ("mu", "D"):
+            getattr(p, k)[0], getattr(p, k)[1] = float(v[0]), float(v[1])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def it_auto_dt(p: it_params, dx_cm: float) -> float:
+    out = ctypes.c_double()
+    _check(lib().it_auto_dt(ctypes.byref(p), float(dx_cm), ctypes.byref(out)))
+    return out.value
+
+
+def it_peak_density(let_keV_um, b_cm, W_eV=34.0) -> float:
+    L, b = _f64(let_keV_um), _f64(b_cm)
+    out = ctypes.c_double()
+    _check(lib().it_peak_density(L.size, _dp(L), _dp(b), float(W_eV), ctypes.byref(out)))
+    return out.value
+
+
+def it_state_bytes(nx, ny, nz, precision=IT_FP32) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().it_state_bytes(it_grid(nx, ny, nz), precision, ctypes.byref(out)))
+    return out.value
+
+
+def it_create(nx, ny, nz, dx_cm, dt_s, p: it_params):
+    h = ctypes.c_void_p()
+    _check(lib().it_create(it_grid(nx, ny, nz), float(dx_cm), float(dt_s), ctypes.byref(p), ctypes.byref(h)))
+    return h
+
+
+def it_create_ex(nx, ny, nz, dx_cm, dt_s, p: it_params, dev_state: int, nbytes: int, stream: int):
+    h = ctypes.c_void_p()
+    _check(lib().it_create_ex(it_grid(nx, ny, nz), float(dx_cm), float(dt_s), ctypes.byref(p),
+                              ctypes.c_void_p(dev_state), nbytes, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def it_deposit_tracks(h, xy_cm, let_keV_um, b_cm):
+    xy, L, b = _f64(xy_cm).reshape(-1), _f64(let_keV_um), _f64(b_cm)
+    _check(lib().it_deposit_tracks(h, L.size, _dp(xy), _dp(L), _dp(b)))
+
+
+def it_deposit_tracks_device(h, n: int, dev_tracks: int):
+    """dev_tracks: device address of n x 4 doubles (x, y, LET, b)."""
+    _check(lib().it_deposit_tracks_device(h, int(n), ctypes.c_void_p(dev_tracks)))
+
+
+def it_schedule_tracks(h, xy_cm, let_keV_um, b_cm, step_idx):
+    xy, L, b = _f64(xy_cm).reshape(-1), _f64(let_keV_um), _f64(b_cm)
+    s = np.ascontiguousarray(step_idx, dtype=np.int64)
+    _check(lib().it_schedule_tracks(h, L.size, _dp(xy), _dp(L), _dp(b),
+                                    s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+
+
+def it_step(h, n_steps: int):
+    _check(lib().it_step(h, int(n_steps)))
+
+
+def it_run_to_completion(h, tol=1e-6, max_steps=10_000_000, check_every=64) -> int:
+    done = ctypes.c_int64()
+    _check(lib().it_run_to_completion(h, float(tol), int(max_steps), int(check_every), ctypes.byref(done)))
+    return done.value
+
+
+def it_tallies(h) -> it_tallies_t:
+    t = it_tallies_t()
+    _check(lib().it_tallies(h, ctypes.byref(t)))
+    return t
+
+
+def it_get_density(h, species: int, out: np.ndarray):
+    _check(lib().it_get_density(h, int(species), out.ctypes.data_as(ctypes.c_void_p), out.nbytes))
+    return out
+
+
+def it_set_density(h, plus: np.ndarray, minus: np.ndarray):
+    _check(lib().it_set_density(h, plus.ctypes.data_as(ctypes.c_void_p), minus.ctypes.data_as(ctypes.c_void_p),
+                                plus.nbytes))
+
+
+def it_device_state(h):
+    p, m, s = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().it_device_state(h, ctypes.byref(p), ctypes.byref(m), ctypes.byref(s)))
+    return p.value, m.value, s.value
+
+
+def it_set_launch(h, kernel=IT_KERNEL_AUTO, tile_rows=0, z_chunks=0, stages=0):
+    _check(lib().it_set_launch(h, int(kernel), int(tile_rows), int(z_chunks), int(stages)))
+
+
+def it_get_launch(h):
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(lib().it_get_launch(h, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("kernel", "tile_rows", "z_chunks", "stages", "ctas"), [x.value for x in v]))
+
+
+def it_destroy(h):
+    if h:
+        _check(lib().it_destroy(h))
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper
+# --------------------------------------------------------------------------
+
+@dataclass
+class Tallies:
+    released: np.ndarray
+    collected_anode: np.ndarray
+    collected_cathode: np.ndarray
+    lost_lateral: np.ndarray
+    in_domain: np.ndarray
+    recombined: float
+    f: float
+    t_s: float
+    dt_s: float
+    steps: int
+    n_min: np.ndarray
+    n_max: np.ndarray
+
+    @property
+    def collected(self):
+        return self.collected_anode + self.collected_cathode
+
+    @classmethod
+    def from_c(cls, t: it_tallies_t):
+        a = lambda x: np.array([x[0], x[1]])
+        return cls(a(t.released), a(t.collected_anode), a(t.collected_cathode), a(t.lost_lateral),
+                   a(t.in_domain), t.recombined, t.f, t.t_s, t.dt_s, t.steps, a(t.n_min), a(t.n_max))
+
+
+class Simulation:
+    """One simulation context on the current CUDA device.
+
+    ``torch_state=True`` allocates the density state as a torch tensor and
+    runs on torch's current stream (``it_create_ex``); otherwise the library
+    owns its memory and stream.
+    """
+
+    def __init__(self, nx, ny, nz, dx_cm, voltage_V, dt_s=0.0, mu=(1.73, 1.87), D=(0.037, 0.037),
+                 alpha=1.6e-6, W_eV=34.0, precision=IT_FP32, lateral_bc=IT_PERIODIC,
+                 scheme=IT_LAX_WENDROFF, kernel=IT_KERNEL_AUTO, n_peak_cm3=0.0, cfl_safety=1.0,
+                 react_kappa=0.5, torch_state=False):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.precision = precision
+        self.p = it_params_default(mu=mu, D=D, alpha=alpha, W_eV=W_eV, gap_cm=self.nz * dx_cm,
+                                   voltage_V=voltage_V, precision=precision, lateral_bc=lateral_bc,
+                                   scheme=scheme, kernel=kernel, n_peak_cm3=n_peak_cm3,
+                                   cfl_safety=cfl_safety, react_kappa=react_kappa)
+        self._state = None
+        if torch_state:
+            import torch
+            nbytes = it_state_bytes(nx, ny, nz, precision)
+            self._state = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            stream = torch.cuda.current_stream().cuda_stream
+            self.h = it_create_ex(nx, ny, nz, dx_cm, dt_s, self.p, self._state.data_ptr(), nbytes, stream)
+        else:
+            self.h = it_create(nx, ny, nz, dx_cm, dt_s, self.p)
+
+    @property
+    def dtype(self):
+        return np.float64 if self.precision == IT_FP64 else np.float32
+
+    def deposit(self, x_cm, y_cm, let_keV_um, b_cm):
+        xy = np.stack([np.asarray(x_cm, np.float64), np.asarray(y_cm, np.float64)], axis=1)
+        it_deposit_tracks(self.h, xy, let_keV_um, b_cm)
+
+    def schedule(self, x_cm, y_cm, let_keV_um, b_cm, step_idx):
+        xy = np.stack([np.asarray(x_cm, np.float64), np.asarray(y_cm, np.float64)], axis=1)
+        it_schedule_tracks(self.h, xy, let_keV_um, b_cm, step_idx)
+
+    def step(self, n=1):
+        it_step(self.h, n)
+
+    def run_to_completion(self, tol=1e-6, max_steps=10_000_000, check_every=64):
+        return it_run_to_completion(self.h, tol, max_steps, check_every)
+
+    def tallies(self) -> Tallies:
+        return Tallies.from_c(it_tallies(self.h))
+
+    def density(self, species) -> np.ndarray:
+        out = np.empty((self.nz, self.ny, self.nx), dtype=self.dtype)
+        return it_get_density(self.h, species, out)
+
+    def set_density(self, plus, minus):
+        shape = (self.nz, self.ny, self.nx)
+        p = np.ascontiguousarray(np.broadcast_to(plus, shape), dtype=self.dtype)
+        m = np.ascontiguousarray(np.broadcast_to(minus, shape), dtype=self.dtype)
+        it_set_density(self.h, p, m)
+
+    def launch(self):
+        return it_get_launch(self.h)
+
+    def set_launch(self, kernel=IT_KERNEL_AUTO, tile_rows=0, z_chunks=0, stages=0):
+        it_set_launch(self.h, kernel, tile_rows, z_chunks, stages)
+
+    def close(self):
+        if getattr(self, "h", None):
+            it_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

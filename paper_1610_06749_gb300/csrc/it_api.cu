@@ -1,0 +1,594 @@
+// it_api.cu -- the C ABI (include/iontracks.h): parameters, time-step rule,
+// context lifetime, deposition, stepping with CUDA-graph segments, tallies.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "it_internal.cuh"
+
+namespace itk {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return IT_ECUDA;
+}
+
+static int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+// Eq. (vNeum) with E along z and dx = dy = dz: 6 s + c^2 <= 1 (Lax-Wendroff)
+// or 6 s + c <= 1 (upwind), s = D dt/dx^2, c = mu E dt/dx.
+static double dt_von_neumann(const it_params *p, double dx) {
+    const double E = p->voltage_V / p->gap_cm;
+    double best = INFINITY;
+    for (int s = 0; s < 2; ++s) {
+        const double q = 6.0 * p->D[s] / (dx * dx);
+        const double v = p->mu[s] * E / dx;
+        double dt;
+        if (p->scheme == IT_UPWIND) {
+            dt = (q + v) > 0 ? 1.0 / (q + v) : INFINITY;
+        } else if (v > 0) {
+            dt = (-q + std::sqrt(q * q + 4.0 * v * v)) / (2.0 * v * v);
+        } else {
+            dt = q > 0 ? 1.0 / q : INFINITY;
+        }
+        best = std::min(best, dt);
+    }
+    return best;
+}
+
+static int check_params(const it_params *p, it_grid g, double dx) {
+    if (!p) return fail(IT_EINVAL, "params is NULL");
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(IT_EINVAL, "grid needs at least one cell per axis");
+    if (!(std::isfinite(dx) && dx > 0)) return fail(IT_EINVAL, "dx must be positive and finite");
+    for (int s = 0; s < 2; ++s)
+        if (!finite_nonneg(p->mu[s]) || !finite_nonneg(p->D[s]))
+            return fail(IT_EINVAL, "mobilities and diffusion constants must be finite and >= 0");
+    if (!finite_nonneg(p->alpha) || !finite_nonneg(p->voltage_V))
+        return fail(IT_EINVAL, "alpha and voltage must be finite and >= 0");
+    if (!(std::isfinite(p->W_eV) && p->W_eV > 0)) return fail(IT_EINVAL, "W must be positive");
+    if (!(std::isfinite(p->gap_cm) && p->gap_cm > 0)) return fail(IT_EINVAL, "gap must be positive");
+    if (std::fabs(p->gap_cm - g.nz * dx) > 1e-9 * p->gap_cm)
+        return fail(IT_EINVAL, "gap_cm must equal nz * dx");
+    if (p->precision != IT_FP32 && p->precision != IT_FP64) return fail(IT_EINVAL, "bad precision");
+    if (p->lateral_bc != IT_PERIODIC && p->lateral_bc != IT_ABSORBING) return fail(IT_EINVAL, "bad lateral_bc");
+    if (p->scheme != IT_LAX_WENDROFF && p->scheme != IT_UPWIND) return fail(IT_EINVAL, "bad scheme");
+    if (p->kernel < IT_KERNEL_AUTO || p->kernel > IT_KERNEL_ZMARCH) return fail(IT_EINVAL, "bad kernel");
+    if (!(std::isfinite(p->cfl_safety) && p->cfl_safety > 0 && p->cfl_safety <= 1.0))
+        return fail(IT_EINVAL, "cfl_safety must be in (0, 1]");
+    if (!(std::isfinite(p->react_kappa) && p->react_kappa > 0)) return fail(IT_EINVAL, "react_kappa must be > 0");
+    if (!finite_nonneg(p->n_peak_cm3)) return fail(IT_EINVAL, "n_peak must be finite and >= 0");
+    return IT_OK;
+}
+
+template <typename T>
+static void make_coef(Coef<T> &cf, const it_params *p, double dx, double dt) {
+    const double E = p->voltage_V / p->gap_cm;
+    const double vol = dx * dx * dx;
+    for (int s = 0; s < 2; ++s) {
+        const double sigma = s == 0 ? 1.0 : -1.0;   // n+ drifts to +z, n- to -z
+        const double c = p->mu[s] * E * dt / dx;
+        const double sd = p->D[s] * dt / (dx * dx);
+        double wzm, wzp;
+        if (p->scheme == IT_UPWIND) {
+            wzm = sd + (sigma > 0 ? c : 0.0);
+            wzp = sd + (sigma > 0 ? 0.0 : c);
+        } else {
+            // Lax-Wendroff: n - (sigma c/2)(n_{k+1} - n_{k-1}) + (c^2/2)(n_{k+1} - 2n + n_{k-1})
+            wzm = sd + 0.5 * c * c + 0.5 * sigma * c;
+            wzp = sd + 0.5 * c * c - 0.5 * sigma * c;
+        }
+        cf.wx[s] = (T)sd;
+        cf.wy[s] = (T)sd;
+        cf.wzm[s] = (T)wzm;
+        cf.wzp[s] = (T)wzp;
+        cf.anode_f[s] = (double)cf.wzp[s] * vol;
+        cf.cathode_f[s] = (double)cf.wzm[s] * vol;
+        cf.latx_f[s] = (double)cf.wx[s] * vol;
+        cf.laty_f[s] = (double)cf.wy[s] * vol;
+    }
+    cf.adt = (T)(p->alpha * dt);
+    cf.rec_f = (double)cf.adt * vol;
+}
+
+static int ctx_free(it_ctx *c) {
+    if (!c) return IT_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->own_state && c->state_base) cudaFree(c->state_base);
+    cudaFree(c->d_slots);
+    cudaFree(c->d_mon);
+    cudaFree(c->d_acc);
+    cudaFree(c->d_out);
+    cudaFree(c->d_plane);
+    cudaFree(c->d_tracks);
+    cudaFree(c->d_wx);
+    cudaFree(c->d_wy);
+    cudaFree(c->d_err);
+    if (c->h_out) cudaFreeHost(c->h_out);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->stage_done) cudaEventDestroy(c->stage_done);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return IT_OK;
+}
+
+static int ensure_tracks(it_ctx *c, int64_t n) {
+    if (n <= c->track_cap) return IT_OK;
+    cudaFree(c->d_tracks); cudaFree(c->d_wx); cudaFree(c->d_wy);
+    c->d_tracks = c->d_wx = c->d_wy = nullptr;
+    c->track_cap = 0;
+    IT_CK(cudaMalloc(&c->d_tracks, sizeof(double) * 4 * n));
+    IT_CK(cudaMalloc(&c->d_wx, sizeof(double) * c->g.nx * n));
+    IT_CK(cudaMalloc(&c->d_wy, sizeof(double) * c->g.ny * n));
+    c->track_cap = n;
+    return IT_OK;
+}
+
+constexpr int64_t kTrackChunk = 8192;
+
+// pinned staging buffer for host track uploads; waits for the previous
+// upload out of it before it is reused
+static int stage_tracks(it_ctx *c, int64_t n, double **out) {
+    if (c->stage_done) IT_CK(cudaEventSynchronize(c->stage_done));
+    if (n > c->stage_cap) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->stage_cap = 0;
+        IT_CK(cudaMallocHost(&c->h_stage, sizeof(double) * 4 * n));
+        c->stage_cap = n;
+    }
+    if (!c->stage_done) IT_CK(cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming));
+    *out = c->h_stage;
+    return IT_OK;
+}
+
+// upload packed tracks [n][4] (pinned host memory) and deposit them, chunk by chunk
+static int deposit_packed(it_ctx *c, const double *packed, int64_t n) {
+    for (int64_t off = 0; off < n; off += kTrackChunk) {
+        const int64_t m = std::min(kTrackChunk, n - off);
+        int rc = ensure_tracks(c, m);
+        if (rc) return rc;
+        IT_CK(cudaMemcpyAsync(c->d_tracks, packed + 4 * off, sizeof(double) * 4 * m,
+                              cudaMemcpyHostToDevice, c->stream));
+        rc = launch_deposit(c, m, c->stream);
+        if (rc) return rc;
+    }
+    if (n > 0 && c->stage_done) IT_CK(cudaEventRecord(c->stage_done, c->stream));
+    return IT_OK;
+}
+
+static int validate_tracks(int64_t n, const double *xy, const double *let, const double *b) {
+    if (n < 0) return fail(IT_EINVAL, "negative track count");
+    if (n > 0 && (!xy || !let || !b)) return fail(IT_EINVAL, "track arrays are NULL");
+    for (int64_t t = 0; t < n; ++t) {
+        if (!std::isfinite(xy[2 * t]) || !std::isfinite(xy[2 * t + 1]))
+            return fail(IT_EINVAL, "track position is not finite");
+        if (!(std::isfinite(let[t]) && let[t] >= 0)) return fail(IT_EINVAL, "LET must be finite and >= 0");
+        if (!(std::isfinite(b[t]) && b[t] > 0)) return fail(IT_EINVAL, "track radius b must be > 0");
+    }
+    return IT_OK;
+}
+
+static int one_step(it_ctx *c) {
+    return c->kernel == IT_KERNEL_ZMARCH ? launch_step_zmarch(c, c->stream) : launch_step_simple(c, c->stream);
+}
+
+constexpr int kGraphSteps = 32;   // even: a segment returns to the same ping-pong set
+
+// run n steps with no deposit in between
+static int run_plain(it_ctx *c, int64_t n) {
+    while (n >= kGraphSteps) {
+        if (!c->graph || c->graph_parity != c->cur) {
+            if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+            const int start = c->cur;
+            cudaGraph_t g = nullptr;
+            IT_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = IT_OK;
+            for (int q = 0; q < kGraphSteps && rc == IT_OK; ++q) rc = one_step(c);
+            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            c->cur = start;   // capture recorded the launches; nothing ran yet
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+            c->graph_parity = start;
+        }
+        IT_CK(cudaGraphLaunch(c->graph, c->stream));
+        n -= kGraphSteps;
+        c->steps += kGraphSteps;
+    }
+    for (int64_t q = 0; q < n; ++q) {
+        int rc = one_step(c);
+        if (rc) return rc;
+        c->steps += 1;
+    }
+    return IT_OK;
+}
+
+}  // namespace itk
+
+using namespace itk;
+
+extern "C" {
+
+const char *it_version(void) { return "iontracks-gb300 0.1 (sm_103a)"; }
+
+const char *it_last_error(void) { return g_err.c_str(); }
+
+int it_params_default(it_params *p) {
+    if (!p) return fail(IT_EINVAL, "params is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->mu[0] = 1.73; p->mu[1] = 1.87;
+    p->D[0] = 0.037; p->D[1] = 0.037;
+    p->alpha = 1.6e-6;
+    p->W_eV = 34.0;
+    p->precision = IT_FP32;
+    p->lateral_bc = IT_PERIODIC;
+    p->scheme = IT_LAX_WENDROFF;
+    p->kernel = IT_KERNEL_AUTO;
+    p->cfl_safety = 1.0;
+    p->react_kappa = 0.5;
+    return IT_OK;
+}
+
+int it_auto_dt(const it_params *p, double dx_cm, double *dt_out) {
+    if (!p || !dt_out) return fail(IT_EINVAL, "NULL argument");
+    if (!(std::isfinite(dx_cm) && dx_cm > 0) || !(p->gap_cm > 0)) return fail(IT_EINVAL, "dx and gap must be > 0");
+    double dt = p->cfl_safety * dt_von_neumann(p, dx_cm);
+    if (p->alpha > 0 && p->n_peak_cm3 > 0) dt = std::min(dt, p->react_kappa / (p->alpha * p->n_peak_cm3));
+    if (!std::isfinite(dt)) return fail(IT_EINVAL, "no finite time step (all transport constants are zero)");
+    *dt_out = dt;
+    return IT_OK;
+}
+
+int it_peak_density(int64_t n, const double *let, const double *b, double W_eV, double *out) {
+    if (!out || n < 0 || (n > 0 && (!let || !b)) || !(W_eV > 0)) return fail(IT_EINVAL, "bad argument");
+    double best = 0.0;
+    for (int64_t t = 0; t < n; ++t) {
+        const double N0 = let[t] * 1e7 / W_eV;
+        best = std::max(best, N0 / (M_PI * b[t] * b[t]));
+    }
+    *out = best;
+    return IT_OK;
+}
+
+int it_state_bytes(it_grid g, int32_t precision, size_t *bytes_out) {
+    if (!bytes_out || g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(IT_EINVAL, "bad grid");
+    const size_t es = precision == IT_FP64 ? 8 : 4;
+    const size_t cells = (size_t)g.nx * g.ny * g.nz;
+    // four arrays, each rounded up to 256 bytes
+    const size_t one = (cells * es + 255) / 256 * 256;
+    *bytes_out = 4 * one;
+    return IT_OK;
+}
+
+int it_create_ex(it_grid g, double dx_cm, double dt_s, const it_params *p, void *dev_state, size_t bytes,
+                 void *stream, it_ctx **out) {
+    if (!out) return fail(IT_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(p, g, dx_cm);
+    if (rc) return rc;
+    double dtmax = 0.0;
+    rc = it_auto_dt(p, dx_cm, &dtmax);
+    if (rc) return rc;
+    double dt = dt_s;
+    if (!(dt_s > 0)) {
+        dt = dtmax;
+    } else {
+        const double vn = dt_von_neumann(p, dx_cm);
+        if (!std::isfinite(dt_s) || dt_s > vn * (1.0 + 1e-12))
+            return fail(IT_EINVAL, "dt exceeds the von Neumann bound of Eq. (vNeum)");
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return fail(IT_ECUDA, "no CUDA device available");
+
+    it_ctx *c = new (std::nothrow) it_ctx();
+    if (!c) return fail(IT_ENOMEM, "host allocation failed");
+    c->g = Grid{g.nx, g.ny, g.nz};
+    c->dx = dx_cm;
+    c->dt = dt;
+    c->p = *p;
+    c->prec = p->precision;
+    c->esize = p->precision == IT_FP64 ? 8 : 4;
+    c->graph_parity = -1;
+
+    auto bail = [&](int code) { ctx_free(c); return code; };
+
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+        c->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+        c->own_stream = true;
+    }
+    size_t need = 0;
+    it_state_bytes(g, p->precision, &need);
+    const size_t one = need / 4;
+    if (dev_state) {
+        if (bytes < need) return bail(fail(IT_EINVAL, "dev_state smaller than it_state_bytes()"));
+        if (((uintptr_t)dev_state & 255) != 0) return bail(fail(IT_EINVAL, "dev_state must be 256-byte aligned"));
+        c->state_base = dev_state;
+        c->own_state = false;
+    } else {
+        e = cudaMalloc(&c->state_base, need);
+        if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? fail(IT_ENOMEM, "state allocation failed")
+                                                                          : cuda_fail(e, "cudaMalloc"));
+        c->own_state = true;
+    }
+    char *base = (char *)c->state_base;
+    c->n[0][0] = base; c->n[0][1] = base + one; c->n[1][0] = base + 2 * one; c->n[1][1] = base + 3 * one;
+    c->cur = 0;
+    e = cudaMemsetAsync(c->state_base, 0, need, c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemset"));
+
+    make_coef(c->cf, p, dx_cm, dt);
+    make_coef(c->cd, p, dx_cm, dt);
+
+    // kernel choice
+    c->kernel = IT_KERNEL_SIMPLE;
+    if (p->kernel == IT_KERNEL_ZMARCH || p->kernel == IT_KERNEL_AUTO) {
+        rc = zmarch_configure(c);
+        if (rc == IT_OK) {
+            c->kernel = IT_KERNEL_ZMARCH;
+        } else if (p->kernel == IT_KERNEL_ZMARCH) {
+            return bail(rc);
+        }
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->nslots = c->kernel == IT_KERNEL_ZMARCH ? c->zm_grid : simple_grid(c);
+    c->nmon = 2 * sms;
+
+    if ((e = cudaMalloc(&c->d_slots, sizeof(double) * NT * c->nslots)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_mon, sizeof(double) * NM * c->nmon)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_acc, sizeof(DevAcc))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_out, sizeof(double) * NOUT)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_plane, sizeof(double) * c->g.plane())) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_out, sizeof(double) * NOUT)) != cudaSuccess)
+        return bail(cuda_fail(e, "scratch allocation"));
+    if ((e = cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_acc, 0, sizeof(DevAcc), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMemset"));
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
+    *out = c;
+    return IT_OK;
+}
+
+int it_create(it_grid g, double dx_cm, double dt_s, const it_params *p, it_ctx **out) {
+    return it_create_ex(g, dx_cm, dt_s, p, nullptr, 0, nullptr, out);
+}
+
+int it_deposit_tracks(it_ctx *c, int64_t n, const double *xy, const double *let, const double *b) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    int rc = validate_tracks(n, xy, let, b);
+    if (rc || n == 0) return rc;
+    double *packed = nullptr;
+    rc = stage_tracks(c, n, &packed);
+    if (rc) return rc;
+    for (int64_t t = 0; t < n; ++t) {
+        packed[4 * t + 0] = xy[2 * t];
+        packed[4 * t + 1] = xy[2 * t + 1];
+        packed[4 * t + 2] = let[t];
+        packed[4 * t + 3] = b[t];
+    }
+    return deposit_packed(c, packed, n);
+}
+
+int it_deposit_tracks_device(it_ctx *c, int64_t n, const double *dev_tracks) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (n < 0 || (n > 0 && !dev_tracks)) return fail(IT_EINVAL, "bad track array");
+    for (int64_t off = 0; off < n; off += kTrackChunk) {
+        const int64_t m = std::min(kTrackChunk, n - off);
+        int rc = ensure_tracks(c, m);
+        if (rc) return rc;
+        IT_CK(cudaMemcpyAsync(c->d_tracks, dev_tracks + 4 * off, sizeof(double) * 4 * m, cudaMemcpyDeviceToDevice,
+                              c->stream));
+        rc = launch_deposit(c, m, c->stream);
+        if (rc) return rc;
+    }
+    return IT_OK;
+}
+
+int it_schedule_tracks(it_ctx *c, int64_t n, const double *xy, const double *let, const double *b,
+                       const int64_t *step_idx) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    int rc = validate_tracks(n, xy, let, b);
+    if (rc) return rc;
+    if (n > 0 && !step_idx) return fail(IT_EINVAL, "step_idx is NULL");
+    for (int64_t t = 0; t < n; ++t)
+        if (step_idx[t] < c->steps) return fail(IT_EINVAL, "a scheduled step has already been taken");
+    std::vector<int64_t> order((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t bb) { return step_idx[a] < step_idx[bb]; });
+    c->sched_step.resize((size_t)n);
+    c->sched_tr.resize((size_t)n * 4);
+    for (int64_t q = 0; q < n; ++q) {
+        const int64_t t = order[q];
+        c->sched_step[q] = step_idx[t];
+        c->sched_tr[4 * q + 0] = xy[2 * t];
+        c->sched_tr[4 * q + 1] = xy[2 * t + 1];
+        c->sched_tr[4 * q + 2] = let[t];
+        c->sched_tr[4 * q + 3] = b[t];
+    }
+    c->sched_ptr = 0;
+    return IT_OK;
+}
+
+int it_step(it_ctx *c, int64_t n) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(IT_EINVAL, "negative step count");
+    const int64_t end = c->steps + n;
+    while (c->steps < end) {
+        // deposit tracks that arrive at the start of this step
+        size_t q = c->sched_ptr;
+        while (q < c->sched_step.size() && c->sched_step[q] == c->steps) ++q;
+        if (q > c->sched_ptr) {
+            const int64_t m = (int64_t)(q - c->sched_ptr);
+            double *packed = nullptr;
+            int rc = stage_tracks(c, m, &packed);
+            if (rc) return rc;
+            std::memcpy(packed, c->sched_tr.data() + 4 * c->sched_ptr, sizeof(double) * 4 * m);
+            rc = deposit_packed(c, packed, m);
+            if (rc) return rc;
+            c->sched_ptr = q;
+        }
+        int64_t until = end;
+        if (c->sched_ptr < c->sched_step.size()) until = std::min(until, c->sched_step[c->sched_ptr]);
+        if (until <= c->steps) until = c->steps + 1;
+        int rc = run_plain(c, until - c->steps);
+        if (rc) return rc;
+    }
+    return IT_OK;
+}
+
+int it_tallies(it_ctx *c, it_tallies_t *t) {
+    if (!c || !t) return fail(IT_EINVAL, "NULL argument");
+    int rc = launch_monitor(c, c->stream);
+    if (rc) return rc;
+    rc = launch_finalize(c, c->stream);
+    if (rc) return rc;
+    IT_CK(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * NOUT, cudaMemcpyDeviceToHost, c->stream));
+    IT_CK(cudaStreamSynchronize(c->stream));
+    const double *o = c->h_out;
+    std::memset(t, 0, sizeof(*t));
+    t->recombined = o[0];
+    t->collected_anode[0] = o[1]; t->collected_anode[1] = o[2];
+    t->collected_cathode[0] = o[3]; t->collected_cathode[1] = o[4];
+    t->lost_lateral[0] = o[5]; t->lost_lateral[1] = o[6];
+    t->in_domain[0] = o[NT]; t->in_domain[1] = o[NT + 1];
+    t->n_min[0] = o[NT + 2]; t->n_min[1] = o[NT + 3];
+    t->n_max[0] = o[NT + 4]; t->n_max[1] = o[NT + 5];
+    t->released[0] = o[NT + NM]; t->released[1] = o[NT + NM + 1];
+    const double rel = t->released[0] + t->released[1];
+    const double col = t->collected_anode[0] + t->collected_anode[1] + t->collected_cathode[0] + t->collected_cathode[1];
+    t->f = rel > 0 ? col / rel : NAN;
+    t->steps = c->steps;
+    t->dt_s = c->dt;
+    t->t_s = c->dt * (double)c->steps;
+    if (o[NT + NM + 2] != 0.0) return fail(IT_ETIMEOUT, "a bounded device wait ran out in the step kernel");
+    return IT_OK;
+}
+
+int it_run_to_completion(it_ctx *c, double tol, int64_t max_steps, int64_t check_every, int64_t *steps_done) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (!(tol >= 0) || max_steps < 0 || check_every < 1) return fail(IT_EINVAL, "bad argument");
+    const int64_t start = c->steps;
+    it_tallies_t t;
+    int rc = IT_OK;
+    for (;;) {
+        rc = it_tallies(c, &t);
+        if (rc) break;
+        if (!std::isfinite(t.in_domain[0] + t.in_domain[1] + t.recombined)) { rc = fail(IT_EUNSTABLE, "state is not finite"); break; }
+        const double rel = t.released[0] + t.released[1];
+        // scheduled tracks still to come keep the run going
+        const bool pending = c->sched_ptr < c->sched_step.size();
+        if (!pending && rel > 0 && (t.in_domain[0] + t.in_domain[1]) / rel < tol) break;
+        if (!pending && rel == 0) break;
+        const int64_t left = start + max_steps - c->steps;
+        if (left <= 0) { rc = fail(IT_ETIMEOUT, "max_steps reached before completion"); break; }
+        rc = it_step(c, std::min(check_every, left));
+        if (rc) break;
+    }
+    if (steps_done) *steps_done = c->steps - start;
+    return rc;
+}
+
+int it_get_density(it_ctx *c, int species, void *dst, size_t bytes) {
+    if (!c || !dst || (species != 0 && species != 1)) return fail(IT_EINVAL, "bad argument");
+    if (bytes != c->g.cells() * c->esize) return fail(IT_EINVAL, "bytes must equal cells * element size");
+    IT_CK(cudaMemcpyAsync(dst, c->n[c->cur][species], bytes, cudaMemcpyDeviceToHost, c->stream));
+    IT_CK(cudaStreamSynchronize(c->stream));
+    return IT_OK;
+}
+
+int it_set_density(it_ctx *c, const void *plus, const void *minus, size_t bytes) {
+    if (!c || !plus || !minus) return fail(IT_EINVAL, "bad argument");
+    if (bytes != c->g.cells() * c->esize) return fail(IT_EINVAL, "bytes must equal cells * element size");
+    IT_CK(cudaMemcpyAsync(c->n[c->cur][0], plus, bytes, cudaMemcpyHostToDevice, c->stream));
+    IT_CK(cudaMemcpyAsync(c->n[c->cur][1], minus, bytes, cudaMemcpyHostToDevice, c->stream));
+    IT_CK(cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream));
+    IT_CK(cudaMemsetAsync(c->d_acc, 0, sizeof(DevAcc), c->stream));
+    c->steps = 0;
+    c->sched_step.clear(); c->sched_tr.clear(); c->sched_ptr = 0;
+    it_tallies_t t;
+    int rc = it_tallies(c, &t);
+    if (rc) return rc;
+    DevAcc a{};
+    a.released[0] = t.in_domain[0];
+    a.released[1] = t.in_domain[1];
+    IT_CK(cudaMemcpyAsync(c->d_acc, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
+    IT_CK(cudaStreamSynchronize(c->stream));
+    return IT_OK;
+}
+
+int it_device_state(it_ctx *c, void **plus, void **minus, void **stream) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (plus) *plus = c->n[c->cur][0];
+    if (minus) *minus = c->n[c->cur][1];
+    if (stream) *stream = (void *)c->stream;
+    return IT_OK;
+}
+
+int it_set_launch(it_ctx *c, int kernel, int tile_rows, int z_chunks, int stages) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (c->steps != 0) return fail(IT_ESTATE, "launch shape can only change before the first step");
+    if (kernel == IT_KERNEL_SIMPLE) {
+        c->kernel = IT_KERNEL_SIMPLE;
+    } else if (kernel == IT_KERNEL_ZMARCH || kernel == IT_KERNEL_AUTO) {
+        int rc = zmarch_setup(c, tile_rows, z_chunks, stages);
+        if (rc) {
+            if (kernel == IT_KERNEL_ZMARCH) return rc;
+            c->kernel = IT_KERNEL_SIMPLE;
+        } else {
+            c->kernel = IT_KERNEL_ZMARCH;
+        }
+    } else {
+        return fail(IT_EINVAL, "bad kernel");
+    }
+    const int n = c->kernel == IT_KERNEL_ZMARCH ? c->zm_grid : simple_grid(c);
+    if (n != c->nslots) {
+        double *ns = nullptr;
+        IT_CK(cudaMalloc(&ns, sizeof(double) * NT * n));
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->d_slots);
+        c->d_slots = ns;
+        c->nslots = n;
+    }
+    IT_CK(cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream));
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return IT_OK;
+}
+
+int it_get_launch(it_ctx *c, int *kernel, int *tile_rows, int *z_chunks, int *stages, int *ctas) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    const bool zm = c->kernel == IT_KERNEL_ZMARCH;
+    if (kernel) *kernel = c->kernel;
+    if (tile_rows) *tile_rows = zm ? c->zm.TY : 0;
+    if (z_chunks) *z_chunks = zm ? c->zm.nzc : 0;
+    if (stages) *stages = zm ? c->zm.S : 0;
+    if (ctas) *ctas = c->nslots;
+    return IT_OK;
+}
+
+int it_destroy(it_ctx *c) { return ctx_free(c); }
+
+}  // extern "C"

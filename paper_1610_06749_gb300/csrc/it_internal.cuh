@@ -1,0 +1,145 @@
+// it_internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/iontracks.h"
+
+namespace itk {
+
+// Tally slots every step kernel writes per CTA (FP64, accumulated over all
+// steps by the CTA that owns the slot, so the fixed-order final reduction is
+// deterministic):
+//   0 recombined ion pairs, 1/2 anode +/-, 3/4 cathode +/-, 5/6 lateral +/-
+constexpr int NT = 8;
+// Monitor values of the current state per CTA: in-domain +/- (ions),
+// min +/-, max +/- (densities).
+constexpr int NM = 6;
+// finalize output: NT tallies, NM monitor values, released +/-, error flag
+constexpr int NOUT = NT + NM + 3;
+
+// Update weights of one species in flux (increment) form:
+//   n' = n + wx((x- - n) + (x+ - n)) + wy((y- - n) + (y+ - n))
+//          + wzm (z- - n) + wzp (z+ - n) - adt n+ n-
+// wzm multiplies the neighbour at k-1, wzp the one at k+1.  With this form
+// the rounded weights still conserve mass exactly in real arithmetic.
+template <typename T>
+struct Coef {
+    T wx[2], wy[2], wzm[2], wzp[2];
+    T adt;            // alpha * dt
+    // FP64 factors that turn per-CTA sums into ions (weights as rounded to T)
+    double rec_f;     // adt * vol
+    double anode_f[2];    // wzp * vol  (cell k=0 sends wzp to the ghost k=-1)
+    double cathode_f[2];  // wzm * vol  (cell k=nz-1 sends wzm to the ghost k=nz)
+    double latx_f[2], laty_f[2];
+};
+
+struct Grid {
+    int nx, ny, nz;
+    size_t plane() const { return (size_t)nx * ny; }
+    size_t cells() const { return plane() * nz; }
+};
+
+// Launch shape of the z-march kernel: a CTA owns TY full-width rows of one
+// y-tile and a chunk of z planes; planes are staged through an S-deep ring
+// of shared-memory slots by TMA.
+struct ZmConf {
+    int TY;           // rows per tile (divides ny)
+    int nzc;          // z chunks
+    int ntile;        // ny / TY
+    int S;            // ring depth (>= 3)
+    int bx;           // TMA box width in x (nx or 256)
+    int nbx;          // nx / bx
+    int reg_top, reg_main, reg_bot;   // float offsets of the halo/main rows in a block
+    int blk;          // floats per (species, x-box) block, 128-byte multiple
+    int slot;         // floats per slot = 2 * nbx * blk
+    unsigned tx_bytes;   // bytes TMA delivers per slot
+    size_t smem;      // dynamic shared memory per CTA
+    int threads;      // 256
+    int ctas_per_sm;
+};
+
+// tallies of one context kept on the device
+struct DevAcc {
+    double released[2];
+    double pad[6];
+};
+
+}  // namespace itk
+
+struct it_ctx {
+    itk::Grid g;
+    double dx, dt;
+    it_params p;
+    int prec;             // IT_FP32 / IT_FP64
+    size_t esize;         // element size
+    void *n[2][2];        // [set][species]
+    int cur;              // current set
+    bool own_state;
+    void *state_base;
+    cudaStream_t stream;
+    bool own_stream;
+    int kernel;           // resolved IT_KERNEL_SIMPLE / IT_KERNEL_ZMARCH
+    int nslots;           // CTAs that own tally slots
+    double *d_slots;      // [nslots][NT]
+    double *d_mon;        // [nmon][NM]
+    int nmon;
+    double *d_acc;        // DevAcc
+    double *d_out;        // finalize output [NT + NM + 2]
+    double *h_out;        // pinned mirror
+    // deposition scratch
+    double *d_plane;      // [ny][nx]
+    double *d_tracks;     // [cap][4]: x, y, LET, b
+    double *d_wx, *d_wy;  // [cap][nx], [cap][ny]
+    int64_t track_cap;
+    double *h_stage;      // pinned staging for host track uploads [stage_cap][4]
+    int64_t stage_cap;
+    cudaEvent_t stage_done;   // last upload from h_stage has completed
+    // schedule (host, sorted by step)
+    std::vector<int64_t> sched_step;
+    std::vector<double> sched_tr;   // [n][4]
+    size_t sched_ptr;
+    int64_t steps;
+    // graph of a fixed segment of steps
+    cudaGraphExec_t graph;
+    int graph_len;
+    int graph_parity;
+    // z-march kernel configuration (it_zmarch.cu)
+    itk::ZmConf zm;
+    int zm_grid;
+    CUtensorMap tm_main[2][2];   // [set][species], box {bx, TY, 1}
+    CUtensorMap tm_halo[2][2];   // [set][species], box {bx, 1, 1}
+    itk::Coef<float> cf;
+    itk::Coef<double> cd;
+    int *d_err;           // device error flag (bounded waits that ran out)
+};
+
+namespace itk {
+
+// thread-local error message
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define IT_CK(call)                                                  \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return itk::cuda_fail(_e, #call);     \
+    } while (0)
+
+// kernels (it_kernels.cu)
+int launch_step_simple(it_ctx *c, cudaStream_t s);
+int launch_step_zmarch(it_ctx *c, cudaStream_t s);
+int zmarch_configure(it_ctx *c);
+int zmarch_setup(it_ctx *c, int want_ty, int want_nzc, int want_s);
+int launch_finalize(it_ctx *c, cudaStream_t s);
+int launch_monitor(it_ctx *c, cudaStream_t s);
+int launch_deposit(it_ctx *c, int64_t n, cudaStream_t s);   // tracks already in d_tracks
+int launch_zero(void *p, size_t bytes, cudaStream_t s);
+int simple_grid(const it_ctx *c);
+
+}  // namespace itk

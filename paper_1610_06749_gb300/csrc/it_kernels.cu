@@ -1,0 +1,334 @@
+// it_kernels.cu -- deposition, the simple step kernel, monitor and tally
+// reduction kernels.
+//
+// Deposition follows Eqs. (linear_density), (Gaussian), (created): a track
+// parallel to E with N0 = LET/W ions per cm and radial profile
+// N0/(pi b^2) exp(-r^2/b^2), integrated over each cell, identical on every z
+// plane.  The step is the Appendix scheme (Lax-Wendroff drift along z, FTCS
+// diffusion on three axes, -alpha n+ n- from the old level), written in flux
+// form so the tallies of what crosses the electrode faces close the charge
+// balance.
+#include <cmath>
+
+#include "it_device.cuh"
+#include "it_internal.cuh"
+
+namespace itk {
+
+// ---------------------------------------------------------------------------
+// simple step: one thread per cell, neighbours read through L1/L2
+// ---------------------------------------------------------------------------
+template <typename T, bool PERIODIC>
+__global__ void __launch_bounds__(256)
+step_simple_kernel(const T *__restrict__ ip, const T *__restrict__ im, T *__restrict__ op,
+                   T *__restrict__ om, int nx, int ny, int nz, Coef<T> c,
+                   double *__restrict__ slots) {
+    __shared__ double red[32 * 7];
+    const size_t plane = (size_t)nx * ny;
+    const size_t total = plane * nz;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % nx);
+        const size_t r = idx / nx;
+        const int j = (int)(r % ny);
+        const int k = (int)(r / ny);
+        const size_t ixm = (i > 0) ? idx - 1 : idx + (nx - 1);
+        const size_t ixp = (i < nx - 1) ? idx + 1 : idx - (nx - 1);
+        const size_t iym = (j > 0) ? idx - nx : idx + (size_t)(ny - 1) * nx;
+        const size_t iyp = (j < ny - 1) ? idx + nx : idx - (size_t)(ny - 1) * nx;
+        const T p0 = ip[idx], m0 = im[idx];
+        const T rr = p0 * m0;
+        acc[0] += (double)rr;
+        const int cx = (i == 0) + (i == nx - 1);
+        const int cy = (j == 0) + (j == ny - 1);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const T *in = s ? im : ip;
+            const T n0 = s ? m0 : p0;
+            const T xm = (PERIODIC || i > 0) ? in[ixm] : T(0);
+            const T xp = (PERIODIC || i < nx - 1) ? in[ixp] : T(0);
+            const T ym = (PERIODIC || j > 0) ? in[iym] : T(0);
+            const T yp = (PERIODIC || j < ny - 1) ? in[iyp] : T(0);
+            const T zm = (k > 0) ? in[idx - plane] : T(0);
+            const T zp = (k < nz - 1) ? in[idx + plane] : T(0);
+            const T v = n0 + c.wx[s] * ((xm - n0) + (xp - n0)) + c.wy[s] * ((ym - n0) + (yp - n0)) +
+                        c.wzm[s] * (zm - n0) + c.wzp[s] * (zp - n0) - c.adt * rr;
+            (s ? om : op)[idx] = v;
+            if (k == 0) acc[1 + s] += (double)n0;
+            if (k == nz - 1) acc[3 + s] += (double)n0;
+            if (!PERIODIC && (cx | cy))
+                acc[5 + s] += (double)n0 * (cx * c.latx_f[s] + cy * c.laty_f[s]);
+        }
+    }
+    block_sum<7>(acc, red);
+    if (threadIdx.x == 0) {
+        double *sl = slots + (size_t)blockIdx.x * NT;
+        sl[0] += acc[0] * c.rec_f;
+        sl[1] += acc[1] * c.anode_f[0];
+        sl[2] += acc[2] * c.anode_f[1];
+        sl[3] += acc[3] * c.cathode_f[0];
+        sl[4] += acc[4] * c.cathode_f[1];
+        sl[5] += acc[5];
+        sl[6] += acc[6];
+    }
+}
+
+int simple_grid(const it_ctx *c) {
+    const size_t blocks = (c->g.cells() + 255) / 256;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t cap = (size_t)sms * 8;
+    return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+}
+
+int launch_step_simple(it_ctx *c, cudaStream_t s) {
+    const int nb = c->nslots;
+    const int cur = c->cur, nxt = cur ^ 1;
+    if (c->prec == IT_FP32) {
+        auto *ip = (const float *)c->n[cur][0], *im = (const float *)c->n[cur][1];
+        auto *op = (float *)c->n[nxt][0], *om = (float *)c->n[nxt][1];
+        if (c->p.lateral_bc == IT_PERIODIC)
+            step_simple_kernel<float, true><<<nb, 256, 0, s>>>(ip, im, op, om, c->g.nx, c->g.ny, c->g.nz, c->cf, c->d_slots);
+        else
+            step_simple_kernel<float, false><<<nb, 256, 0, s>>>(ip, im, op, om, c->g.nx, c->g.ny, c->g.nz, c->cf, c->d_slots);
+    } else {
+        auto *ip = (const double *)c->n[cur][0], *im = (const double *)c->n[cur][1];
+        auto *op = (double *)c->n[nxt][0], *om = (double *)c->n[nxt][1];
+        if (c->p.lateral_bc == IT_PERIODIC)
+            step_simple_kernel<double, true><<<nb, 256, 0, s>>>(ip, im, op, om, c->g.nx, c->g.ny, c->g.nz, c->cd, c->d_slots);
+        else
+            step_simple_kernel<double, false><<<nb, 256, 0, s>>>(ip, im, op, om, c->g.nx, c->g.ny, c->g.nz, c->cd, c->d_slots);
+    }
+    IT_CK(cudaGetLastError());
+    c->cur = nxt;
+    return IT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// monitor: in-domain ions and extreme densities of the current state
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+monitor_kernel(const T *__restrict__ ip, const T *__restrict__ im, size_t total, double vol,
+               double *__restrict__ mon) {
+    __shared__ double red[32 * 2];
+    __shared__ double rmin[32 * 2], rmax[32 * 2];
+    double sum[2] = {0, 0};
+    double mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const double a = (double)ip[idx], b = (double)im[idx];
+        sum[0] += a; sum[1] += b;
+        mn[0] = fmin(mn[0], a); mn[1] = fmin(mn[1], b);
+        mx[0] = fmax(mx[0], a); mx[1] = fmax(mx[1], b);
+        // a NaN propagates through the sum and is reported by the host
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[q] = fmin(mn[q], __shfl_down_sync(0xffffffffu, mn[q], o));
+            mx[q] = fmax(mx[q], __shfl_down_sync(0xffffffffu, mx[q], o));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        rmin[warp * 2] = mn[0]; rmin[warp * 2 + 1] = mn[1];
+        rmax[warp * 2] = mx[0]; rmax[warp * 2 + 1] = mx[1];
+    }
+    block_sum<2>(sum, red);   // contains the __syncthreads for rmin/rmax too
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int w = 1; w < nw; ++w) {
+            mn[0] = fmin(mn[0], rmin[w * 2]); mn[1] = fmin(mn[1], rmin[w * 2 + 1]);
+            mx[0] = fmax(mx[0], rmax[w * 2]); mx[1] = fmax(mx[1], rmax[w * 2 + 1]);
+        }
+        double *m = mon + (size_t)blockIdx.x * NM;
+        m[0] = sum[0] * vol; m[1] = sum[1] * vol;
+        m[2] = mn[0]; m[3] = mn[1]; m[4] = mx[0]; m[5] = mx[1];
+    }
+}
+
+int launch_monitor(it_ctx *c, cudaStream_t s) {
+    const double vol = c->dx * c->dx * c->dx;
+    const int cur = c->cur;
+    if (c->prec == IT_FP32)
+        monitor_kernel<float><<<c->nmon, 256, 0, s>>>((const float *)c->n[cur][0], (const float *)c->n[cur][1],
+                                                     c->g.cells(), vol, c->d_mon);
+    else
+        monitor_kernel<double><<<c->nmon, 256, 0, s>>>((const double *)c->n[cur][0], (const double *)c->n[cur][1],
+                                                      c->g.cells(), vol, c->d_mon);
+    IT_CK(cudaGetLastError());
+    return IT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// finalize: fixed-order sums of the per-CTA slots and monitor values
+//   out[0..NT) tallies, out[NT..NT+NM) monitor, out[NT+NM..+2) released
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+finalize_kernel(const double *__restrict__ slots, int nslots, const double *__restrict__ mon,
+                int nmon, const double *__restrict__ acc, const int *__restrict__ err, double *__restrict__ out) {
+    __shared__ double red[32 * (NT + 2)];
+    __shared__ double rmin[32 * 2], rmax[32 * 2];
+    double v[NT + 2];
+#pragma unroll
+    for (int q = 0; q < NT + 2; ++q) v[q] = 0.0;
+    for (int b = threadIdx.x; b < nslots; b += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < NT; ++q) v[q] += slots[(size_t)b * NT + q];
+    }
+    double mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nmon; b += blockDim.x) {
+        v[NT] += mon[(size_t)b * NM + 0];
+        v[NT + 1] += mon[(size_t)b * NM + 1];
+        mn[0] = fmin(mn[0], mon[(size_t)b * NM + 2]); mn[1] = fmin(mn[1], mon[(size_t)b * NM + 3]);
+        mx[0] = fmax(mx[0], mon[(size_t)b * NM + 4]); mx[1] = fmax(mx[1], mon[(size_t)b * NM + 5]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[q] = fmin(mn[q], __shfl_down_sync(0xffffffffu, mn[q], o));
+            mx[q] = fmax(mx[q], __shfl_down_sync(0xffffffffu, mx[q], o));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        rmin[warp * 2] = mn[0]; rmin[warp * 2 + 1] = mn[1];
+        rmax[warp * 2] = mx[0]; rmax[warp * 2 + 1] = mx[1];
+    }
+    block_sum<NT + 2>(v, red);
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int w = 1; w < nw; ++w) {
+            mn[0] = fmin(mn[0], rmin[w * 2]); mn[1] = fmin(mn[1], rmin[w * 2 + 1]);
+            mx[0] = fmax(mx[0], rmax[w * 2]); mx[1] = fmax(mx[1], rmax[w * 2 + 1]);
+        }
+        for (int q = 0; q < NT; ++q) out[q] = v[q];
+        out[NT + 0] = v[NT]; out[NT + 1] = v[NT + 1];
+        out[NT + 2] = mn[0]; out[NT + 3] = mn[1]; out[NT + 4] = mx[0]; out[NT + 5] = mx[1];
+        out[NT + NM + 0] = acc[0];
+        out[NT + NM + 1] = acc[1];
+        out[NT + NM + 2] = (double)*err;
+    }
+}
+
+int launch_finalize(it_ctx *c, cudaStream_t s) {
+    finalize_kernel<<<1, 256, 0, s>>>(c->d_slots, c->nslots, c->d_mon, c->nmon, c->d_acc, c->d_err, c->d_out);
+    IT_CK(cudaGetLastError());
+    return IT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// deposition
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long floor_div(long long a, long long n) {
+    return (a >= 0) ? a / n : -((-a + n - 1) / n);
+}
+
+// Per track and axis: the fraction of the 1D Gaussian factor
+// exp(-u^2/b^2)/(sqrt(pi) b) that falls in each cell, summed over the
+// periodic images of the cell inside the window +-ceil(6 b/dx) around the
+// centre cell (absorbing faces: only the cell itself, if inside).
+__global__ void deposit_tables_kernel(const double *__restrict__ tr, double dx, int nx, int ny,
+                                      int periodic, double *__restrict__ wx, double *__restrict__ wy) {
+    const long long t = blockIdx.x;
+    const int axis = blockIdx.y;
+    const int n = axis ? ny : nx;
+    const double ctr = tr[t * 4 + axis];
+    const double b = tr[t * 4 + 3];
+    const long long w = (long long)ceil(6.0 * b / dx);
+    const long long ic = (long long)floor(ctr / dx);
+    const long long lo = ic - w, hi = ic + w;
+    double *out = axis ? (wy + t * ny) : (wx + t * nx);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double sum = 0.0;
+        if (periodic) {
+            long long ii = i + n * (-floor_div(-(lo - i), n));   // first image >= lo
+            for (; ii <= hi; ii += n)
+                sum += 0.5 * (erf(((double)(ii + 1) * dx - ctr) / b) - erf(((double)ii * dx - ctr) / b));
+        } else if (i >= lo && i <= hi) {
+            sum = 0.5 * (erf(((double)(i + 1) * dx - ctr) / b) - erf(((double)i * dx - ctr) / b));
+        }
+        out[i] = sum;
+    }
+}
+
+// plane[j][i] = sum_t N0_t wx[t][i] wy[t][j] / dx^2, tracks in index order.
+__global__ void deposit_plane_kernel(const double *__restrict__ tr, const double *__restrict__ wx,
+                                     const double *__restrict__ wy, long long nt, int nx, int ny,
+                                     double inv_dx2, double inv_W, double *__restrict__ plane) {
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= (long long)nx * ny) return;
+    const int i = (int)(cell % nx), j = (int)(cell / nx);
+    double sum = 0.0;
+    for (long long t = 0; t < nt; ++t) {
+        const double a = wx[t * nx + i];
+        if (a == 0.0) continue;
+        const double bb = wy[t * ny + j];
+        if (bb == 0.0) continue;
+        const double N0 = tr[t * 4 + 2] * 1e7 * inv_W;   // ions per cm
+        sum += N0 * a * bb;
+    }
+    plane[cell] = sum * inv_dx2;
+}
+
+template <typename T>
+__global__ void deposit_apply_kernel(T *__restrict__ p, T *__restrict__ m, const double *__restrict__ plane,
+                                     size_t plane_n, size_t total) {
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const double a = plane[idx % plane_n];
+        p[idx] = (T)((double)p[idx] + a);
+        m[idx] = (T)((double)m[idx] + a);
+    }
+}
+
+// released += sum(plane) * dx^2 * (nz dx) for both species, fixed order
+__global__ void __launch_bounds__(256)
+deposit_released_kernel(const double *__restrict__ plane, size_t n, double factor, double *__restrict__ acc) {
+    __shared__ double red[32];
+    double v[1] = {0.0};
+    for (size_t q = threadIdx.x; q < n; q += blockDim.x) v[0] += plane[q];
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) {
+        acc[0] += v[0] * factor;
+        acc[1] += v[0] * factor;
+    }
+}
+
+int launch_deposit(it_ctx *c, int64_t n, cudaStream_t s) {
+    if (n <= 0) return IT_OK;
+    const int nx = c->g.nx, ny = c->g.ny;
+    dim3 gt((unsigned)n, 2);
+    deposit_tables_kernel<<<gt, 128, 0, s>>>(c->d_tracks, c->dx, nx, ny, c->p.lateral_bc == IT_PERIODIC,
+                                            c->d_wx, c->d_wy);
+    IT_CK(cudaGetLastError());
+    const long long pn = (long long)nx * ny;
+    deposit_plane_kernel<<<(unsigned)((pn + 255) / 256), 256, 0, s>>>(
+        c->d_tracks, c->d_wx, c->d_wy, n, nx, ny, 1.0 / (c->dx * c->dx), 1.0 / c->p.W_eV, c->d_plane);
+    IT_CK(cudaGetLastError());
+    const size_t total = c->g.cells();
+    const int nb = c->nmon;
+    if (c->prec == IT_FP32)
+        deposit_apply_kernel<float><<<nb, 256, 0, s>>>((float *)c->n[c->cur][0], (float *)c->n[c->cur][1],
+                                                       c->d_plane, (size_t)pn, total);
+    else
+        deposit_apply_kernel<double><<<nb, 256, 0, s>>>((double *)c->n[c->cur][0], (double *)c->n[c->cur][1],
+                                                        c->d_plane, (size_t)pn, total);
+    IT_CK(cudaGetLastError());
+    const double factor = c->dx * c->dx * (c->dx * c->g.nz);
+    deposit_released_kernel<<<1, 256, 0, s>>>(c->d_plane, (size_t)pn, factor, c->d_acc);
+    IT_CK(cudaGetLastError());
+    return IT_OK;
+}
+
+int launch_zero(void *p, size_t bytes, cudaStream_t s) {
+    IT_CK(cudaMemsetAsync(p, 0, bytes, s));
+    return IT_OK;
+}
+
+}  // namespace itk

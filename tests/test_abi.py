@@ -1,0 +1,103 @@
+"""The C-ABI library builds, loads and exports what include/iontracks.h
+declares; host-only entry points work without a GPU and agree with the
+oracle's time-step rule; device entry points fail loudly without a GPU."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle.oracle as o
+from paper_1610_06749_gb300 import build as libbuild
+from paper_1610_06749_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "iontracks.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    libbuild.build()
+    return B.lib()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(it_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for want in ["it_create", "it_create_ex", "it_deposit_tracks", "it_schedule_tracks", "it_step",
+                 "it_tallies", "it_destroy", "it_run_to_completion", "it_get_density", "it_set_density",
+                 "it_auto_dt", "it_last_error"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol(L):
+    for n in declared_symbols():
+        assert hasattr(B, n), n
+
+
+def test_version_and_defaults(L):
+    assert "sm_103a" in B.it_version()
+    p = B.it_params_default()
+    assert tuple(p.mu) == (1.73, 1.87) and tuple(p.D) == (0.037, 0.037)
+    assert p.alpha == 1.6e-6 and p.W_eV == 34.0 and p.react_kappa == 0.5
+
+
+@pytest.mark.parametrize("scheme", [B.IT_LAX_WENDROFF, B.IT_UPWIND])
+@pytest.mark.parametrize("dx,V,d", [(2e-4, 200.0, 0.02), (5e-4, 50.0, 0.2), (8e-4, 300.0, 0.2048)])
+def test_auto_dt_matches_oracle_rule(L, scheme, dx, V, d):
+    npk = o.peak_track_density([1000.0], [1e-3])
+    for n_peak in (0.0, npk):
+        p = B.it_params_default(gap_cm=d, voltage_V=V, scheme=scheme, n_peak_cm3=n_peak)
+        got = B.it_auto_dt(p, dx)
+        want = o.dt_rule(dx, V, d, (1.73, 1.87), (0.037, 0.037), 1.6e-6, n_peak=n_peak,
+                         scheme=o.SCHEME_UPWIND if scheme == B.IT_UPWIND else o.SCHEME_LAX_WENDROFF)
+        assert got == pytest.approx(want, rel=1e-14)
+
+
+def test_peak_density_and_state_bytes(L):
+    let, b = np.array([1.0, 1000.0, 10.0]), np.array([1e-3, 1e-3, 5e-4])
+    assert B.it_peak_density(let, b) == pytest.approx(o.peak_track_density(let, b), rel=1e-15)
+    n = B.it_state_bytes(256, 256, 400, B.IT_FP32)
+    assert n == 4 * 256 * 256 * 400 * 4
+    assert B.it_state_bytes(48, 48, 100, B.IT_FP64) == 4 * ((48 * 48 * 100 * 8 + 255) // 256 * 256)
+
+
+def test_invalid_parameters_are_rejected(L):
+    p = B.it_params_default(gap_cm=0.02, voltage_V=200.0)
+    with pytest.raises(B.ItError) as e:
+        B.it_auto_dt(p, -1.0)
+    assert e.value.code == B.IT_EINVAL
+    p2 = B.it_params_default(gap_cm=0.021, voltage_V=200.0)      # gap != nz * dx
+    with pytest.raises(B.ItError) as e:
+        B.it_create(48, 48, 100, 2e-4, 0.0, p2)
+    assert e.value.code == B.IT_EINVAL
+    p3 = B.it_params_default(gap_cm=0.02, voltage_V=float("nan"))
+    with pytest.raises(B.ItError) as e:
+        B.it_create(48, 48, 100, 2e-4, 0.0, p3)
+    assert e.value.code == B.IT_EINVAL
+    # dt above the von Neumann bound
+    dt = B.it_auto_dt(p, 2e-4)
+    with pytest.raises(B.ItError) as e:
+        B.it_create(48, 48, 100, 2e-4, dt * 1.01, p)
+    assert e.value.code == B.IT_EINVAL
+
+
+def test_create_without_gpu_fails_loudly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = B.it_params_default(gap_cm=0.02, voltage_V=200.0)
+    with pytest.raises(B.ItError) as e:
+        B.it_create(48, 48, 100, 2e-4, 0.0, p)
+    assert e.value.code == B.IT_ECUDA

@@ -1,0 +1,259 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Densities: max|n_gpu - n_orc| / max|n_orc| <= 1e-4 per species, and the
+pointwise relative error <= 1e-4 wherever n_orc > 1e-3 max (FP32 storage);
+FP64 storage: 1e-12.  f within 1e-5 absolute (FP32) or 1e-12 (FP64).  Sizes
+span several tiles and ragged tails; the full-size workloads run in the
+launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle.oracle as o
+from paper_1610_06749_gb300 import binding as B
+from paper_1610_06749_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MU, DD, ALPHA = (1.73, 1.87), (0.037, 0.037), 1.6e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1610_06749_gb300 import build
+    build.build()
+    B.lib()
+
+
+def assert_density_close(gpu, orc, tol):
+    scale = np.max(np.abs(orc))
+    if scale == 0:
+        assert np.max(np.abs(gpu)) == 0
+        return
+    err = np.max(np.abs(gpu.astype(np.float64) - orc)) / scale
+    assert err <= tol, f"max abs error / max = {err:.3e} > {tol}"
+    big = np.abs(orc) > 1e-3 * scale
+    rel = np.max(np.abs(gpu[big].astype(np.float64) - orc[big]) / np.abs(orc[big]))
+    assert rel <= tol, f"pointwise relative error {rel:.3e} > {tol}"
+
+
+def make_pair(nx, ny, nz, dx, V, tracks, precision=B.IT_FP32, lateral=B.IT_PERIODIC,
+              scheme=B.IT_LAX_WENDROFF, kernel=B.IT_KERNEL_AUTO, mu=MU, D=DD, alpha=ALPHA, dt=None):
+    if dt is None:
+        npk = o.peak_track_density(tracks.let_keV_um, tracks.b_cm) if len(tracks) else 0.0
+        dt = o.dt_rule(dx, V, nz * dx, mu, D, alpha, n_peak=npk,
+                       scheme=o.SCHEME_UPWIND if scheme == B.IT_UPWIND else o.SCHEME_LAX_WENDROFF)
+    g = B.Simulation(nx, ny, nz, dx, V, dt_s=dt, mu=mu, D=D, alpha=alpha, precision=precision,
+                     lateral_bc=lateral, scheme=scheme, kernel=kernel)
+    O = o.Oracle(nx, ny, nz, dx, dt, mu=mu, D=D, alpha=alpha, voltage_V=V,
+                 lateral_bc=o.LATERAL_ABSORBING if lateral == B.IT_ABSORBING else o.LATERAL_PERIODIC,
+                 scheme=o.SCHEME_UPWIND if scheme == B.IT_UPWIND else o.SCHEME_LAX_WENDROFF)
+    return g, O
+
+
+def compare_tallies(tg, to, f_tol, rel_tol):
+    assert tg.f == pytest.approx(to.f, abs=f_tol)
+    for name in ("released", "in_domain"):
+        np.testing.assert_allclose(getattr(tg, name), getattr(to, name), rtol=rel_tol)
+    tot = to.released.sum()
+    for name in ("collected_anode", "collected_cathode", "lost_lateral"):
+        np.testing.assert_allclose(getattr(tg, name), getattr(to, name), rtol=0, atol=rel_tol * tot)
+    assert tg.recombined == pytest.approx(to.recombined, abs=rel_tol * tot)
+
+
+CASES = [
+    # nx, ny, nz, dx, V, lateral, scheme, kernel, n_tracks
+    (36, 20, 23, 5e-4, 200.0, B.IT_PERIODIC, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH, 7),
+    (36, 20, 23, 5e-4, 200.0, B.IT_ABSORBING, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH, 7),
+    (64, 48, 40, 4e-4, 100.0, B.IT_PERIODIC, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH, 25),
+    (64, 48, 40, 4e-4, 100.0, B.IT_ABSORBING, B.IT_UPWIND, B.IT_KERNEL_ZMARCH, 25),
+    (256, 16, 12, 5e-4, 300.0, B.IT_PERIODIC, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH, 40),
+    (512, 8, 10, 5e-4, 300.0, B.IT_ABSORBING, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH, 40),
+    (37, 19, 13, 5e-4, 200.0, B.IT_PERIODIC, B.IT_LAX_WENDROFF, B.IT_KERNEL_SIMPLE, 6),
+    (37, 19, 13, 5e-4, 200.0, B.IT_ABSORBING, B.IT_UPWIND, B.IT_KERNEL_SIMPLE, 6),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}-bc{c[5]}-s{c[6]}-k{c[7]}")
+def test_small_grids_match_oracle(case):
+    nx, ny, nz, dx, V, lat, sch, ker, nt = case
+    tr = synth.uniform_tracks(100 + nx + ny, nt, nx * dx, ny * dx, 1e-3, let="loguniform")
+    # push a few tracks onto the faces so deposits wrap or clip
+    tr.x_cm[0] = 0.2 * dx
+    tr.y_cm[0] = (ny - 0.3) * dx
+    g, O = make_pair(nx, ny, nz, dx, V, tr, lateral=lat, scheme=sch, kernel=ker)
+    with g:
+        assert g.launch()["kernel"] == ker
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        done = 0
+        for chk in (1, 7, 40, 75):
+            g.step(chk - done)
+            O.step(chk - done)
+            done = chk
+            for s in range(2):
+                assert_density_close(g.density(s), O.density(s), 1e-4)
+        compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
+
+
+@pytest.mark.parametrize("lat", [B.IT_PERIODIC, B.IT_ABSORBING])
+def test_fp64_storage_matches_oracle_to_rounding(lat):
+    nx, ny, nz, dx, V = 24, 20, 30, 5e-4, 150.0
+    tr = synth.uniform_tracks(9, 5, nx * dx, ny * dx, 1e-3)
+    g, O = make_pair(nx, ny, nz, dx, V, tr, precision=B.IT_FP64, lateral=lat)
+    with g:
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        g.step(60)
+        O.step(60)
+        for s in range(2):
+            assert_density_close(g.density(s), O.density(s), 1e-12)
+        compare_tallies(g.tallies(), O.tallies(), 1e-12, 1e-12)
+
+
+def test_single_track_48x48x100_fp64_matches_oracle_f():
+    w = synth.single_track_48x48x100()
+    tr = synth.single_track_tracks(w)
+    g, O = make_pair(w.nx, w.ny, w.nz, w.dx_cm, w.voltage_V, tr, precision=B.IT_FP64, lateral=B.IT_ABSORBING)
+    with g:
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        steps = g.run_to_completion(tol=1e-9, check_every=32)
+        O.step(steps)
+        tg, to = g.tallies(), O.tallies()
+        assert tg.in_domain.sum() / tg.released.sum() < 1e-9
+        assert tg.f == pytest.approx(to.f, abs=1e-12)
+        # the single-track f sits above Jaffe's Gaussian-ansatz value at this
+        # LET (y1 = 0.02); the oracle pins cover where the ansatz holds
+        assert 0.44 < tg.f < 0.46
+
+
+def test_fp32_single_track_f_within_1e5():
+    w = synth.single_track_48x48x100()
+    tr = synth.single_track_tracks(w)
+    g, O = make_pair(w.nx, w.ny, w.nz, w.dx_cm, w.voltage_V, tr, precision=B.IT_FP32, lateral=B.IT_ABSORBING)
+    with g:
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        steps = g.run_to_completion(tol=1e-9, check_every=32)
+        O.step(steps)
+        assert g.tallies().f == pytest.approx(O.tallies().f, abs=1e-5)
+
+
+def test_gpu_conservation_and_determinism():
+    nx, ny, nz, dx = 128, 64, 80, 5e-4
+    tr = synth.uniform_tracks(21, 120, nx * dx, ny * dx, 1e-3)
+    dt = o.dt_rule(dx, 100.0, nz * dx, n_peak=o.peak_track_density(tr.let_keV_um, tr.b_cm))
+    runs = []
+    for _ in range(2):
+        with B.Simulation(nx, ny, nz, dx, 100.0, dt_s=dt) as g:
+            g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+            g.step(300)
+            t = g.tallies()
+            for s in range(2):
+                tot = t.in_domain[s] + t.collected[s] + t.lost_lateral[s] + t.recombined
+                assert tot == pytest.approx(t.released[s], rel=2e-6)
+            runs.append((g.density(0), g.density(1), t))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2].f == runs[1][2].f and runs[0][2].recombined == runs[1][2].recombined
+
+
+def test_kernels_agree_and_empty_deposit_is_a_noop():
+    nx, ny, nz, dx = 64, 32, 24, 5e-4
+    tr = synth.uniform_tracks(4, 10, nx * dx, ny * dx, 1e-3)
+    dt = o.dt_rule(dx, 200.0, nz * dx, n_peak=o.peak_track_density(tr.let_keV_um, tr.b_cm))
+    out = []
+    for ker in (B.IT_KERNEL_SIMPLE, B.IT_KERNEL_ZMARCH):
+        with B.Simulation(nx, ny, nz, dx, 200.0, dt_s=dt, kernel=ker) as g:
+            g.deposit([], [], [], [])
+            assert g.tallies().released.sum() == 0.0
+            g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+            g.step(50)
+            out.append((g.density(0), g.tallies()))
+    scale = np.max(np.abs(out[0][0]))
+    assert np.max(np.abs(out[0][0] - out[1][0])) / scale < 1e-6
+    assert out[0][1].f == pytest.approx(out[1][1].f, abs=1e-7)
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 1), (8, 1, 16), (256, 256, 2), (4, 12, 3)])
+def test_degenerate_grids(shape):
+    nx, ny, nz = shape
+    dx = 5e-4
+    tr = synth.uniform_tracks(2, 3, nx * dx, ny * dx, 1e-3, let=5.0)
+    g, O = make_pair(nx, ny, nz, dx, 100.0, tr)
+    with g:
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        g.step(9)
+        O.step(9)
+        for s in range(2):
+            assert_density_close(g.density(s), O.density(s), 1e-4)
+        compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
+
+
+def test_boag_slab_on_gpu():
+    # laterally uniform slab: f = ln(1+u)/u within the front-broadening
+    # residual, and the oracle within 1e-5
+    nz, dx, V, u = 400, 5e-4, 200.0, 2.0
+    d = nz * dx
+    n = u * (MU[0] + MU[1]) * V / (ALPHA * d * d)
+    dt = o.dt_rule(dx, V, d, n_peak=n)
+    g, O = make_pair(4, 4, nz, dx, V, synth.TrackList(*(np.zeros(0),) * 4), dt=dt)
+    with g:
+        f = np.full((nz, 4, 4), n)
+        g.set_density(f, f)
+        O.set_density(f, f)
+        steps = g.run_to_completion(tol=1e-9, check_every=256)
+        O.step(steps)
+        tg = g.tallies()
+        assert tg.f == pytest.approx(o.boag_2vm(u), abs=1e-2)
+        assert tg.f == pytest.approx(O.tallies().f, abs=1e-5)
+
+
+def test_scheduled_tracks_match_oracle_schedule():
+    nx, ny, nz, dx = 64, 64, 32, 8e-4
+    dt = o.dt_rule(dx, 300.0, nz * dx, n_peak=o.peak_track_density([200.0], [1e-3]))
+    tr = synth.poisson_tracks(5, 1e10, nx * dx, ny * dx, dt, 120, 1e-3, synth.CONTINUOUS_LET)
+    assert 10 < len(tr) < 200
+    g, O = make_pair(nx, ny, nz, dx, 300.0, tr, dt=dt)
+    with g:
+        g.schedule(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step)
+        g.step(70)
+        g.step(50)
+        O.run_schedule(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step, 120)
+        for s in range(2):
+            assert_density_close(g.density(s), O.density(s), 1e-4)
+        compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
+
+
+@pytest.mark.parametrize("V", [50.0, 400.0])
+def test_pulsed_256x256x400_full_size(V):
+    # the benchmark workload: 2000 tracks, log-uniform LET, z-march kernel in
+    # its automatic launch shape; full arrays compared after a few steps
+    w = synth.pulsed_256x256x400(V)
+    tr = synth.pulsed_tracks(w)
+    g, O = make_pair(w.nx, w.ny, w.nz, w.dx_cm, V, tr)
+    with g:
+        assert g.launch()["kernel"] == B.IT_KERNEL_ZMARCH
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        g.step(3)
+        O.step(3)
+        for s in range(2):
+            assert_density_close(g.density(s), O.density(s), 1e-4)
+        compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
+
+
+def test_continuous_512x512x256_full_size():
+    w = synth.continuous_512x512x256()
+    dt = o.dt_rule(w.dx_cm, w.voltage_V, w.gap_cm, n_peak=o.peak_track_density([200.0], [1e-3]))
+    tr = synth.poisson_tracks(w.seed, 1e7 * 300, w.nx * w.dx_cm, w.ny * w.dx_cm, dt, 3, w.b_cm,
+                              synth.CONTINUOUS_LET)
+    g, O = make_pair(w.nx, w.ny, w.nz, w.dx_cm, w.voltage_V, tr, dt=dt)
+    with g:
+        g.schedule(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step)
+        g.step(3)
+        O.run_schedule(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step, 3)
+        for s in range(2):
+            assert_density_close(g.density(s), O.density(s), 1e-4)
+        compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
