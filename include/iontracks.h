@@ -201,18 +201,23 @@ int it_get_density(it_ctx *ctx, int species, void *host_dst, size_t bytes);
  * becomes the FP64 sum of what was set, the step counter returns to 0. */
 int it_set_density(it_ctx *ctx, const void *plus, const void *minus, size_t bytes);
 
+/* Return the context to its freshly created state without reallocating:
+ * densities zero, all tallies zero, step counter 0, schedule cleared.
+ * Asynchronous on the context stream (no host synchronisation). */
+int it_reset(it_ctx *ctx);
+
 /* Device pointers of the current n+ and n- fields (valid until the next
  * it_step) and the context's stream (a cudaStream_t). */
 int it_device_state(it_ctx *ctx, void **plus, void **minus, void **stream);
 
 /* Choose the step kernel and, for IT_KERNEL_ZMARCH, its launch shape: rows
- * per tile (a divisor of ny), z chunks per column and ring depth (3..8);
+ * per tile (a divisor of ny), resident CTAs per SM and ring depth (3..16);
  * 0 leaves a value to the built-in rule.  Only before the first step
  * (IT_ESTATE otherwise).  IT_EINVAL if the shape does not fit the grid. */
-int it_set_launch(it_ctx *ctx, int kernel, int tile_rows, int z_chunks, int stages);
+int it_set_launch(it_ctx *ctx, int kernel, int tile_rows, int ctas_per_sm, int stages);
 
 /* Report the kernel in use, its launch shape and its CTA count. */
-int it_get_launch(it_ctx *ctx, int *kernel, int *tile_rows, int *z_chunks, int *stages, int *ctas);
+int it_get_launch(it_ctx *ctx, int *kernel, int *tile_rows, int *ctas_per_sm, int *stages, int *ctas);
 
 /* Destroy a context; NULL is a no-op.  Synchronises the stream first. */
 int it_destroy(it_ctx *ctx);

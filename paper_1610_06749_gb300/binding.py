@@ -85,6 +85,7 @@ def lib():
             "it_tallies": (I, [P, ctypes.POINTER(it_tallies_t)]),
             "it_get_density": (I, [P, I, P, SZ]),
             "it_set_density": (I, [P, P, P, SZ]),
+            "it_reset": (I, [P]),
             "it_device_state": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),
             "it_set_launch": (I, [P, I, I, I, I]),
             "it_get_launch": (I, [P, IP, IP, IP, IP, IP]),
@@ -210,20 +211,24 @@ def it_set_density(h, plus: np.ndarray, minus: np.ndarray):
                                 plus.nbytes))
 
 
+def it_reset(h):
+    _check(lib().it_reset(h))
+
+
 def it_device_state(h):
     p, m, s = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     _check(lib().it_device_state(h, ctypes.byref(p), ctypes.byref(m), ctypes.byref(s)))
     return p.value, m.value, s.value
 
 
-def it_set_launch(h, kernel=IT_KERNEL_AUTO, tile_rows=0, z_chunks=0, stages=0):
-    _check(lib().it_set_launch(h, int(kernel), int(tile_rows), int(z_chunks), int(stages)))
+def it_set_launch(h, kernel=IT_KERNEL_AUTO, tile_rows=0, ctas_per_sm=0, stages=0):
+    _check(lib().it_set_launch(h, int(kernel), int(tile_rows), int(ctas_per_sm), int(stages)))
 
 
 def it_get_launch(h):
     v = [ctypes.c_int() for _ in range(5)]
     _check(lib().it_get_launch(h, *[ctypes.byref(x) for x in v]))
-    return dict(zip(("kernel", "tile_rows", "z_chunks", "stages", "ctas"), [x.value for x in v]))
+    return dict(zip(("kernel", "tile_rows", "ctas_per_sm", "stages", "ctas"), [x.value for x in v]))
 
 
 def it_destroy(h):
@@ -320,11 +325,14 @@ class Simulation:
         m = np.ascontiguousarray(np.broadcast_to(minus, shape), dtype=self.dtype)
         it_set_density(self.h, p, m)
 
+    def reset(self):
+        it_reset(self.h)
+
     def launch(self):
         return it_get_launch(self.h)
 
-    def set_launch(self, kernel=IT_KERNEL_AUTO, tile_rows=0, z_chunks=0, stages=0):
-        it_set_launch(self.h, kernel, tile_rows, z_chunks, stages)
+    def set_launch(self, kernel=IT_KERNEL_AUTO, tile_rows=0, ctas_per_sm=0, stages=0):
+        it_set_launch(self.h, kernel, tile_rows, ctas_per_sm, stages)
 
     def close(self):
         if getattr(self, "h", None):

@@ -73,6 +73,13 @@ static int check_params(const it_params *p, it_grid g, double dx) {
     return IT_OK;
 }
 
+// Round w onto the grid max(q, ulp_T(w)), T having `mant` significand bits.
+static double round_to_grid(double w, double q, int mant) {
+    const double u = w == 0.0 ? q : std::ldexp(1.0, std::ilogb(std::fabs(w)) - (mant - 1));
+    const double g = std::max(q, u);
+    return std::nearbyint(w / g) * g;
+}
+
 template <typename T>
 static void make_coef(Coef<T> &cf, const it_params *p, double dx, double dt) {
     const double E = p->voltage_V / p->gap_cm;
@@ -90,8 +97,22 @@ static void make_coef(Coef<T> &cf, const it_params *p, double dx, double dt) {
             wzm = sd + 0.5 * c * c + 0.5 * sigma * c;
             wzp = sd + 0.5 * c * c - 0.5 * sigma * c;
         }
-        cf.wx[s] = (T)sd;
-        cf.wy[s] = (T)sd;
+        double wx = sd, wy = sd;
+        double w0 = 1.0 - (2.0 * wx + 2.0 * wy + wzm + wzp);
+        if (sizeof(T) == 4) {
+            // common grid q = ulp_f32(w0) (w0 >= 2^-20 assumed for the grid; smaller
+            // w0 uses 2^-43) so that 1 - sum is exact and representable in FP32
+            const int e0 = w0 > 0 ? std::max(std::ilogb(w0), -20) : -20;
+            const double q = std::ldexp(1.0, e0 - 23);
+            wx = round_to_grid(wx, q, 24);
+            wy = round_to_grid(wy, q, 24);
+            wzm = round_to_grid(wzm, q, 24);
+            wzp = round_to_grid(wzp, q, 24);
+            w0 = 1.0 - (2.0 * wx + 2.0 * wy + wzm + wzp);   // exact in FP64
+        }
+        cf.w0[s] = (T)w0;
+        cf.wx[s] = (T)wx;
+        cf.wy[s] = (T)wy;
         cf.wzm[s] = (T)wzm;
         cf.wzp[s] = (T)wzp;
         cf.anode_f[s] = (double)cf.wzp[s] * vol;
@@ -540,6 +561,18 @@ int it_set_density(it_ctx *c, const void *plus, const void *minus, size_t bytes)
     return IT_OK;
 }
 
+int it_reset(it_ctx *c) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    const size_t bytes = c->g.cells() * c->esize;
+    IT_CK(cudaMemsetAsync(c->n[c->cur][0], 0, bytes, c->stream));
+    IT_CK(cudaMemsetAsync(c->n[c->cur][1], 0, bytes, c->stream));
+    IT_CK(cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream));
+    IT_CK(cudaMemsetAsync(c->d_acc, 0, sizeof(DevAcc), c->stream));
+    c->steps = 0;
+    c->sched_step.clear(); c->sched_tr.clear(); c->sched_ptr = 0;
+    return IT_OK;
+}
+
 int it_device_state(it_ctx *c, void **plus, void **minus, void **stream) {
     if (!c) return fail(IT_EINVAL, "ctx is NULL");
     if (plus) *plus = c->n[c->cur][0];
@@ -548,13 +581,13 @@ int it_device_state(it_ctx *c, void **plus, void **minus, void **stream) {
     return IT_OK;
 }
 
-int it_set_launch(it_ctx *c, int kernel, int tile_rows, int z_chunks, int stages) {
+int it_set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages) {
     if (!c) return fail(IT_EINVAL, "ctx is NULL");
     if (c->steps != 0) return fail(IT_ESTATE, "launch shape can only change before the first step");
     if (kernel == IT_KERNEL_SIMPLE) {
         c->kernel = IT_KERNEL_SIMPLE;
     } else if (kernel == IT_KERNEL_ZMARCH || kernel == IT_KERNEL_AUTO) {
-        int rc = zmarch_setup(c, tile_rows, z_chunks, stages);
+        int rc = zmarch_setup(c, tile_rows, ctas_per_sm, stages);
         if (rc) {
             if (kernel == IT_KERNEL_ZMARCH) return rc;
             c->kernel = IT_KERNEL_SIMPLE;
@@ -578,12 +611,12 @@ int it_set_launch(it_ctx *c, int kernel, int tile_rows, int z_chunks, int stages
     return IT_OK;
 }
 
-int it_get_launch(it_ctx *c, int *kernel, int *tile_rows, int *z_chunks, int *stages, int *ctas) {
+int it_get_launch(it_ctx *c, int *kernel, int *tile_rows, int *ctas_per_sm, int *stages, int *ctas) {
     if (!c) return fail(IT_EINVAL, "ctx is NULL");
     const bool zm = c->kernel == IT_KERNEL_ZMARCH;
     if (kernel) *kernel = c->kernel;
     if (tile_rows) *tile_rows = zm ? c->zm.TY : 0;
-    if (z_chunks) *z_chunks = zm ? c->zm.nzc : 0;
+    if (ctas_per_sm) *ctas_per_sm = zm ? c->zm.ctas_per_sm : 0;
     if (stages) *stages = zm ? c->zm.S : 0;
     if (ctas) *ctas = c->nslots;
     return IT_OK;

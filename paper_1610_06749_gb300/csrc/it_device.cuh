@@ -31,4 +31,27 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *smem /* [32][N
     }
 }
 
+// One cell of the update in the weight form of Coef (the same operation
+// sequence in every kernel, so all kernels round identically).
+__device__ __forceinline__ float upd7(float n, float l, float r, float u, float d, float zm, float zp, float rr,
+                                      float w0, float wx, float wy, float wzm, float wzp, float adt) {
+    float v = w0 * n;
+    v = __fmaf_rn(wx, l + r, v);
+    v = __fmaf_rn(wy, u + d, v);
+    v = __fmaf_rn(wzm, zm, v);
+    v = __fmaf_rn(wzp, zp, v);
+    return __fmaf_rn(-adt, rr, v);
+}
+
+__device__ __forceinline__ double upd7(double n, double l, double r, double u, double d, double zm, double zp,
+                                       double rr, double w0, double wx, double wy, double wzm, double wzp,
+                                       double adt) {
+    double v = w0 * n;
+    v = __fma_rn(wx, l + r, v);
+    v = __fma_rn(wy, u + d, v);
+    v = __fma_rn(wzm, zm, v);
+    v = __fma_rn(wzp, zp, v);
+    return __fma_rn(-adt, rr, v);
+}
+
 }  // namespace itk

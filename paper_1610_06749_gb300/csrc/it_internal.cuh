@@ -23,14 +23,16 @@ constexpr int NM = 6;
 // finalize output: NT tallies, NM monitor values, released +/-, error flag
 constexpr int NOUT = NT + NM + 3;
 
-// Update weights of one species in flux (increment) form:
-//   n' = n + wx((x- - n) + (x+ - n)) + wy((y- - n) + (y+ - n))
-//          + wzm (z- - n) + wzp (z+ - n) - adt n+ n-
-// wzm multiplies the neighbour at k-1, wzp the one at k+1.  With this form
-// the rounded weights still conserve mass exactly in real arithmetic.
+// Update weights of one species:
+//   n' = w0 n + wx (x- + x+) + wy (y- + y+) + wzm z- + wzp z+ - adt n+ n-
+// wzm multiplies the neighbour at k-1, wzp the one at k+1.  For FP32 the
+// weights are rounded onto a common grid so that w0 + 2wx + 2wy + wzm + wzp
+// is exactly 1 with every weight exactly representable: the rounded scheme
+// then conserves charge exactly in real arithmetic (only per-operation
+// rounding remains), at a relative perturbation of the weights below 1e-6.
 template <typename T>
 struct Coef {
-    T wx[2], wy[2], wzm[2], wzp[2];
+    T w0[2], wx[2], wy[2], wzm[2], wzp[2];
     T adt;            // alpha * dt
     // FP64 factors that turn per-CTA sums into ions (weights as rounded to T)
     double rec_f;     // adt * vol
@@ -45,12 +47,12 @@ struct Grid {
     size_t cells() const { return plane() * nz; }
 };
 
-// Launch shape of the z-march kernel: a CTA owns TY full-width rows of one
-// y-tile and a chunk of z planes; planes are staged through an S-deep ring
-// of shared-memory slots by TMA.
+// Launch shape of the z-march kernel: tiles of TY full-width rows; each CTA
+// takes a contiguous range of (tile, plane) pairs and streams the planes
+// through an S-deep ring of shared-memory slots by TMA.
 struct ZmConf {
     int TY;           // rows per tile (divides ny)
-    int nzc;          // z chunks
+    int nzc;          // CTAs in the grid (each takes a contiguous range of tile-planes)
     int ntile;        // ny / TY
     int S;            // ring depth (>= 3)
     int bx;           // TMA box width in x (nx or 256)

@@ -52,8 +52,7 @@ step_simple_kernel(const T *__restrict__ ip, const T *__restrict__ im, T *__rest
             const T yp = (PERIODIC || j < ny - 1) ? in[iyp] : T(0);
             const T zm = (k > 0) ? in[idx - plane] : T(0);
             const T zp = (k < nz - 1) ? in[idx + plane] : T(0);
-            const T v = n0 + c.wx[s] * ((xm - n0) + (xp - n0)) + c.wy[s] * ((ym - n0) + (yp - n0)) +
-                        c.wzm[s] * (zm - n0) + c.wzp[s] * (zp - n0) - c.adt * rr;
+            const T v = upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.w0[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
             (s ? om : op)[idx] = v;
             if (k == 0) acc[1 + s] += (double)n0;
             if (k == nz - 1) acc[3 + s] += (double)n0;

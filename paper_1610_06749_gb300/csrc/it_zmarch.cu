@@ -82,22 +82,41 @@ __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, uin
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-// one cell of the flux-form update (same expression as the simple kernel)
-__device__ __forceinline__ float upd(float n, float l, float r, float u, float d, float zm, float zp, float rr,
-                                     float wx, float wy, float wzm, float wzp, float adt) {
-    return n + wx * ((l - n) + (r - n)) + wy * ((u - n) + (d - n)) + wzm * (zm - n) + wzp * (zp - n) - adt * rr;
-}
-
 struct ZmMaps {
     CUtensorMap main[2];   // n+, n- of the input set
     CUtensorMap halo[2];
 };
 
-constexpr int ZM_THREADS = 256;
-constexpr int ZM_MAX_IPT = 4;    // float4 items per thread
+constexpr int ZM_NCW = 16;                       // consumer warps
+constexpr int ZM_CT = ZM_NCW * 32;               // consumer threads
+constexpr int ZM_THREADS = ZM_CT + 32;           // + one producer warp
+constexpr int ZM_MAX_IPT = 4;                    // float4 items per consumer thread
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Position in the ring: slot index and the parity of its current phase.
+struct RingPos {
+    int slot;
+    uint32_t phase;
+    __device__ __forceinline__ void advance(int S) {
+        if (++slot == S) { slot = 0; phase ^= 1u; }
+    }
+};
+
+// Warp-specialised persistent step kernel.
+//   warp ZM_NCW (producer): lane 0 streams the planes this CTA needs into an
+//     S-deep ring with TMA; full[slot] completes when a plane's bytes land,
+//     empty[slot] when all consumer warps have released it.
+//   warps 0..ZM_NCW-1 (consumers): march up z, one plane per iteration,
+//     without block-wide barriers.
+// Work: the tile-planes (y-tile t, plane z) in the order t*nz + z are split
+// into gridDim.x equal contiguous ranges, one per CTA; a range may cover the
+// end of one tile column and the start of the next (each such segment loads
+// its own z-1 / z1 halo planes).
 template <bool PERIODIC, int IPT>
-__global__ void __launch_bounds__(ZM_THREADS)
+__global__ void __launch_bounds__(ZM_THREADS, 1)
 step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp, float *__restrict__ outm,
                    int nx, int ny, int nz, const ZmConf zc, const Coef<float> cf, double *__restrict__ slots,
                    int *__restrict__ err) {
@@ -105,241 +124,263 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     // TMA destinations need 128-byte alignment: round the base up explicitly
     unsigned char *smem_base = zm_smem_raw + ((128u - (smem_u32(zm_smem_raw) & 127u)) & 127u);
     float *ring = reinterpret_cast<float *>(smem_base);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_base + (size_t)zc.S * zc.slot * sizeof(float));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_base + (size_t)zc.S * zc.slot * sizeof(float));
+    uint64_t *empty = full + zc.S;
     __shared__ double red[32 * 7];
+    __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int tile = blockIdx.x % zc.ntile;
-    const int chunk = blockIdx.x / zc.ntile;
-    const int y0 = tile * zc.TY;
-    const int z0 = (int)(((long long)chunk * nz) / zc.nzc);
-    const int z1 = (int)(((long long)(chunk + 1) * nz) / zc.nzc);
-    const int zs = z0 > 0 ? z0 - 1 : 0;          // first plane loaded
-    const int ze = z1 < nz ? z1 : nz - 1;         // last plane loaded
-    const bool has_top = PERIODIC || y0 > 0;
-    const bool has_bot = PERIODIC || y0 + zc.TY < ny;
-    const int ytop = y0 > 0 ? y0 - 1 : ny - 1;
-    const int ybot = y0 + zc.TY < ny ? y0 + zc.TY : 0;
-    const uint32_t tx = 2u * zc.nbx * (uint32_t)(zc.TY + has_top + has_bot) * zc.bx * 4u;
+    const int warp = tid >> 5;
     const int ncol4 = nx >> 2;
     const int nitems = ncol4 * zc.TY;
+    const int S = zc.S;
+    const long long total = (long long)zc.ntile * nz;
+    const long long g0 = total * blockIdx.x / gridDim.x;
+    const long long g1 = total * (blockIdx.x + 1) / gridDim.x;
 
     if (tid == 0) {
-        for (int q = 0; q < zc.S; ++q) mbar_init(&bars[q], 1);
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], ZM_NCW);
+        }
+        abort_flag = 0;
         fence_mbar_init();
     }
-    if (!(has_top && has_bot)) {
-        // absorbing faces: halo rows outside the domain stay zero for the whole kernel
-        for (int q = tid; q < zc.S * 2 * zc.nbx; q += ZM_THREADS) {
-            float *blk = ring + (size_t)(q / (2 * zc.nbx)) * zc.slot + (size_t)(q % (2 * zc.nbx)) * zc.blk;
-            for (int e = 0; e < zc.bx; ++e) {
-                if (!has_top) blk[zc.reg_top + e] = 0.0f;
-                if (!has_bot) blk[zc.reg_bot + e] = 0.0f;
-            }
-        }
-    }
-    fence_proxy_async();
     __syncthreads();
 
-    // issue the TMA loads of plane p into its ring slot (thread 0 only)
-    auto issue = [&](int p) {
-        const int sl = (p - zs) % zc.S;
-        float *base = ring + (size_t)sl * zc.slot;
-        mbar_arrive_expect_tx(&bars[sl], tx);
-        for (int s = 0; s < 2; ++s) {
-            for (int b = 0; b < zc.nbx; ++b) {
-                float *blk = base + (size_t)(s * zc.nbx + b) * zc.blk;
-                tma_load3(blk + zc.reg_main, &maps.main[s], &bars[sl], b * zc.bx, y0, p);
-                if (has_top) tma_load3(blk + zc.reg_top, &maps.halo[s], &bars[sl], b * zc.bx, ytop, p);
-                if (has_bot) tma_load3(blk + zc.reg_bot, &maps.halo[s], &bars[sl], b * zc.bx, ybot, p);
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+
+    if (warp == ZM_NCW) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            RingPos pos{0, 0u};
+            uint32_t issued = 0;
+            bool ok = true;
+            for (long long L = g0; L < g1 && ok;) {
+                const int t = (int)(L / nz), za = (int)(L % nz);
+                const int zb = (int)min((long long)nz, za + (g1 - L));
+                L += zb - za;
+                const int y0 = t * zc.TY;
+                const bool has_top = PERIODIC || y0 > 0;
+                const bool has_bot = PERIODIC || y0 + zc.TY < ny;
+                const int ytop = y0 > 0 ? y0 - 1 : ny - 1;
+                const int ybot = y0 + zc.TY < ny ? y0 + zc.TY : 0;
+                const uint32_t tx = 2u * zc.nbx * (uint32_t)(zc.TY + has_top + has_bot) * zc.bx * 4u;
+                const int lo = za > 0 ? za - 1 : 0, hi = zb < nz ? zb : nz - 1;
+                for (int p = lo; p <= hi; ++p) {
+                    // reuse of a slot waits until all consumers released its previous plane
+                    if (issued >= (uint32_t)S) {
+                        if (abort_flag || !mbar_wait_bounded(&empty[pos.slot], pos.phase ^ 1u)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    float *base = ring + (size_t)pos.slot * zc.slot;
+                    mbar_arrive_expect_tx(&full[pos.slot], tx);
+                    for (int s = 0; s < 2; ++s) {
+                        for (int b = 0; b < zc.nbx; ++b) {
+                            float *blk = base + (size_t)(s * zc.nbx + b) * zc.blk;
+                            tma_load3(blk + zc.reg_main, &maps.main[s], &full[pos.slot], b * zc.bx, y0, p);
+                            if (has_top)
+                                tma_load3(blk + zc.reg_top, &maps.halo[s], &full[pos.slot], b * zc.bx, ytop, p);
+                            if (has_bot)
+                                tma_load3(blk + zc.reg_bot, &maps.halo[s], &full[pos.slot], b * zc.bx, ybot, p);
+                        }
+                    }
+                    ++issued;
+                    pos.advance(S);
+                }
+            }
+            if (!ok) {
+                abort_flag = 1;
+                atomicExch(err, 1);
+                // every issued load must land before the CTA may exit: wait
+                // (bounded) for the last phase issued on each slot
+                for (int j = 0; j < S; ++j) {
+                    if ((uint32_t)j >= issued) break;
+                    const uint32_t ph = j < pos.slot ? pos.phase : (pos.phase ^ 1u);
+                    (void)mbar_wait_bounded(&full[j], ph);
+                }
             }
         }
-    };
-    auto slot_of = [&](int p) { return ring + (size_t)((p - zs) % zc.S) * zc.slot; };
-    auto parity_of = [&](int p) { return (uint32_t)(((p - zs) / zc.S) & 1); };
-    auto wait_plane = [&](int p) { return mbar_wait_bounded(&bars[(p - zs) % zc.S], parity_of(p)); };
-    // pointer to row r (0 = top halo, 1..TY main, TY+1 bottom halo) of a block
-    auto row_ptr = [&](const float *blk, int r) -> const float * {
-        return blk + (r == 0 ? zc.reg_top : (r == zc.TY + 1 ? zc.reg_bot : zc.reg_main + (r - 1) * zc.bx));
-    };
-
-    int issued_hi = zs - 1;   // highest plane issued
-    if (tid == 0) {
-        for (int p = zs; p <= ze && p < zs + zc.S; ++p) issue(p);
-    }
-    issued_hi = min(ze, zs + zc.S - 1);
-
-    // per-item coordinates
-    int ity[IPT], ic4[IPT], ixb[IPT], ixi[IPT];
-    bool ivalid[IPT];
-#pragma unroll
-    for (int it = 0; it < IPT; ++it) {
-        const int q = tid + it * ZM_THREADS;
-        ivalid[it] = q < nitems;
-        const int qe = ivalid[it] ? q : nitems - 1;
-        ity[it] = qe / ncol4;
-        ic4[it] = qe - ity[it] * ncol4;
-        const int x0 = 4 * ic4[it];
-        ixb[it] = x0 / zc.bx;
-        ixi[it] = x0 - ixb[it] * zc.bx;
-    }
-
-    float4 prev[IPT][2], cur[IPT][2];
-    bool failed = false;
-    // centre values of plane p for every item
-    auto load_centre = [&](int p, float4 (&dst)[IPT][2]) {
-        const float *base = slot_of(p);
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int ct = tid;                       // 0 .. ZM_CT-1
+        // per-item offsets inside a species block (species 1: + nbx*blk)
+        int o_c[IPT], o_u[IPT], o_d[IPT], o_l[IPT], o_r[IPT], ty_[IPT], c4_[IPT];
+        bool valid[IPT], need_l[IPT], need_r[IPT], zero_l[IPT], zero_r[IPT];
 #pragma unroll
         for (int it = 0; it < IPT; ++it) {
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const float *blk = base + (size_t)(s * zc.nbx + ixb[it]) * zc.blk;
-                dst[it][s] = *reinterpret_cast<const float4 *>(row_ptr(blk, ity[it] + 1) + ixi[it]);
-            }
+            const int q = ct + it * ZM_CT;
+            valid[it] = q < nitems;
+            const int qe = valid[it] ? q : nitems - 1;
+            const int ty = qe / ncol4, c4 = qe - (qe / ncol4) * ncol4;
+            ty_[it] = ty;
+            c4_[it] = c4;
+            const int x0 = 4 * c4;
+            const int xb = x0 / zc.bx, xi = x0 - xb * zc.bx;
+            const int bofs = xb * zc.blk;
+            o_c[it] = bofs + zc.reg_main + ty * zc.bx + xi;
+            o_u[it] = bofs + (ty == 0 ? zc.reg_top : zc.reg_main + (ty - 1) * zc.bx) + xi;
+            o_d[it] = bofs + (ty == zc.TY - 1 ? zc.reg_bot : zc.reg_main + (ty + 1) * zc.bx) + xi;
+            // x neighbours come by shuffle from the adjacent lane, except where
+            // that lane is outside the warp or the row: then one scalar is read
+            // from shared memory (wrapped at a periodic row end, zero at an
+            // absorbing one)
+            const bool row_start = c4 == 0, row_end = c4 == ncol4 - 1;
+            need_l[it] = lane == 0 || row_start;
+            need_r[it] = lane == 31 || row_end;
+            zero_l[it] = !PERIODIC && row_start;
+            zero_r[it] = !PERIODIC && row_end;
+            const int xl = row_start ? nx - 1 : x0 - 1;
+            const int xr = row_end ? 0 : x0 + 4;
+            o_l[it] = (xl / zc.bx) * zc.blk + zc.reg_main + ty * zc.bx + (xl % zc.bx);
+            o_r[it] = (xr / zc.bx) * zc.blk + zc.reg_main + ty * zc.bx + (xr % zc.bx);
         }
-    };
-
-    // prologue: plane z0-1 (registers only) and plane z0
-    if (z0 > 0) {
-        failed |= !wait_plane(z0 - 1);
-        load_centre(z0 - 1, prev);
-    } else {
-#pragma unroll
-        for (int it = 0; it < IPT; ++it) prev[it][0] = prev[it][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    failed |= !wait_plane(z0);
-    load_centre(z0, cur);
-    if (__syncthreads_or(failed)) goto abort_path;
-    if (z0 > 0 && issued_hi + 1 <= ze) {
-        // the slot of plane z0-1 is free: refill it
-        if (tid == 0) {
-            fence_proxy_async();
-            issue(issued_hi + 1);
-        }
-        ++issued_hi;
-    }
-
-    {
-        double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+        const int sp_ofs = zc.nbx * zc.blk;
+        const size_t plane = (size_t)nx * ny;
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k = z0; k < z1; ++k) {
-            const bool has_next = k + 1 <= nz - 1;
-            if (has_next) failed |= !wait_plane(k + 1);
-            {   // computed even after a lost wait (shuffles need the whole warp); stores are skipped
-                const float *sk = slot_of(k);
-                const float *sn = has_next ? slot_of(k + 1) : nullptr;
-                float rsum = 0.f, an[2] = {0.f, 0.f}, ca[2] = {0.f, 0.f}, lx[2] = {0.f, 0.f}, ly[2] = {0.f, 0.f};
+        RingPos pos{0, 0u};
+        bool failed = false;
+
+        // a lost wait marks the whole warp failed, so shuffles stay convergent
+        auto wait_full = [&](const RingPos &u) {
+            const bool bad = failed || abort_flag || !mbar_wait_bounded(&full[u.slot], u.phase);
+            failed = __any_sync(0xffffffffu, bad);
+        };
+        auto release = [&](const RingPos &u) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[u.slot]);
+        };
+
+        for (long long L = g0; L < g1;) {
+            const int t = (int)(L / nz), za = (int)(L % nz);
+            const int zb = (int)min((long long)nz, za + (g1 - L));
+            L += zb - za;
+            const int y0 = t * zc.TY;
+            float4 prev[IPT][2], cur[IPT][2];
+            size_t off[IPT];
+            bool zero_u[IPT], zero_d[IPT], lat_y[IPT];
+#pragma unroll
+            for (int it = 0; it < IPT; ++it) {
+                const int yg = y0 + ty_[it];
+                off[it] = ((size_t)za * ny + yg) * nx + 4 * c4_[it];
+                zero_u[it] = !PERIODIC && yg == 0;
+                zero_d[it] = !PERIODIC && yg == ny - 1;
+                lat_y[it] = zero_u[it] || zero_d[it];
+            }
+            if (za > 0) {
+                wait_full(pos);
+                const float *sl = ring + (size_t)pos.slot * zc.slot;
+#pragma unroll
+                for (int it = 0; it < IPT; ++it) {
+                    prev[it][0] = *reinterpret_cast<const float4 *>(sl + o_c[it]);
+                    prev[it][1] = *reinterpret_cast<const float4 *>(sl + sp_ofs + o_c[it]);
+                }
+                release(pos);
+                pos.advance(S);
+            } else {
+#pragma unroll
+                for (int it = 0; it < IPT; ++it) prev[it][0] = prev[it][1] = zero4;
+            }
+            wait_full(pos);
+            RingPos pc = pos;
+            pos.advance(S);
+            {
+                const float *sl = ring + (size_t)pc.slot * zc.slot;
+#pragma unroll
+                for (int it = 0; it < IPT; ++it) {
+                    cur[it][0] = *reinterpret_cast<const float4 *>(sl + o_c[it]);
+                    cur[it][1] = *reinterpret_cast<const float4 *>(sl + sp_ofs + o_c[it]);
+                }
+            }
+            float rsum = 0.f;
+            int nacc = 0;
+            for (int k = za; k < zb; ++k) {
+                const bool has_next = k + 1 < nz;
+                if (has_next) wait_full(pos);
+                const float *sk = ring + (size_t)pc.slot * zc.slot;
+                const float *sn = ring + (size_t)pos.slot * zc.slot;
+                float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
 #pragma unroll
                 for (int it = 0; it < IPT; ++it) {
                     const float4 P = cur[it][0], M = cur[it][1];
                     const float4 rr = make_float4(P.x * M.x, P.y * M.y, P.z * M.z, P.w * M.w);
-                    const int ty = ity[it], c4 = ic4[it];
-                    const int yg = y0 + ty;
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
+                        const float *bk = sk + s * sp_ofs;
                         const float4 n = cur[it][s];
-                        const float *blk = sk + (size_t)(s * zc.nbx + ixb[it]) * zc.blk;
-                        const float4 u = *reinterpret_cast<const float4 *>(row_ptr(blk, ty) + ixi[it]);
-                        const float4 d = *reinterpret_cast<const float4 *>(row_ptr(blk, ty + 2) + ixi[it]);
-                        float4 zp = zero4;
-                        if (has_next) {
-                            const float *nb = sn + (size_t)(s * zc.nbx + ixb[it]) * zc.blk;
-                            zp = *reinterpret_cast<const float4 *>(row_ptr(nb, ty + 1) + ixi[it]);
-                        }
-                        // x neighbours: shuffles within the row, shared memory at segment ends
+                        float4 u = *reinterpret_cast<const float4 *>(bk + o_u[it]);
+                        float4 d = *reinterpret_cast<const float4 *>(bk + o_d[it]);
+                        const float4 zp = has_next ? *reinterpret_cast<const float4 *>(sn + s * sp_ofs + o_c[it]) : zero4;
+                        if (zero_u[it]) u = zero4;
+                        if (zero_d[it]) d = zero4;
                         float l = __shfl_up_sync(0xffffffffu, n.w, 1);
                         float r = __shfl_down_sync(0xffffffffu, n.x, 1);
-                        if (c4 == 0) {
-                            if (PERIODIC) {
-                                const int xg = nx - 1;
-                                const float *bb = sk + (size_t)(s * zc.nbx + xg / zc.bx) * zc.blk;
-                                l = row_ptr(bb, ty + 1)[xg % zc.bx];
-                            } else {
-                                l = 0.f;
-                            }
-                        } else if (lane == 0) {
-                            const int xg = 4 * c4 - 1;
-                            const float *bb = sk + (size_t)(s * zc.nbx + xg / zc.bx) * zc.blk;
-                            l = row_ptr(bb, ty + 1)[xg % zc.bx];
-                        }
-                        if (c4 == ncol4 - 1) {
-                            if (PERIODIC) {
-                                const float *bb = sk + (size_t)(s * zc.nbx) * zc.blk;
-                                r = row_ptr(bb, ty + 1)[0];
-                            } else {
-                                r = 0.f;
-                            }
-                        } else if (lane == 31) {
-                            const int xg = 4 * c4 + 4;
-                            const float *bb = sk + (size_t)(s * zc.nbx + xg / zc.bx) * zc.blk;
-                            r = row_ptr(bb, ty + 1)[xg % zc.bx];
-                        }
+                        if (need_l[it]) l = zero_l[it] ? 0.f : bk[o_l[it]];
+                        if (need_r[it]) r = zero_r[it] ? 0.f : bk[o_r[it]];
                         const float4 zm = prev[it][s];
-                        const float wx = cf.wx[s], wy = cf.wy[s], wzm = cf.wzm[s], wzp = cf.wzp[s], adt = cf.adt;
+                        const float w0 = cf.w0[s], wx = cf.wx[s], wy = cf.wy[s], wzm = cf.wzm[s], wzp = cf.wzp[s];
+                        const float adt = cf.adt;
                         float4 v;
-                        v.x = upd(n.x, l, n.y, u.x, d.x, zm.x, zp.x, rr.x, wx, wy, wzm, wzp, adt);
-                        v.y = upd(n.y, n.x, n.z, u.y, d.y, zm.y, zp.y, rr.y, wx, wy, wzm, wzp, adt);
-                        v.z = upd(n.z, n.y, n.w, u.z, d.z, zm.z, zp.z, rr.z, wx, wy, wzm, wzp, adt);
-                        v.w = upd(n.w, n.z, r, u.w, d.w, zm.w, zp.w, rr.w, wx, wy, wzm, wzp, adt);
-                        if (ivalid[it] && !failed) {
-                            float *dst = (s ? outm : outp) + ((size_t)k * ny + yg) * nx + 4 * c4;
-                            *reinterpret_cast<float4 *>(dst) = v;
-                            const float nsum = (n.x + n.y) + (n.z + n.w);
-                            if (k == 0) an[s] += nsum;
-                            if (k == nz - 1) ca[s] += nsum;
+                        v.x = upd7(n.x, l, n.y, u.x, d.x, zm.x, zp.x, rr.x, w0, wx, wy, wzm, wzp, adt);
+                        v.y = upd7(n.y, n.x, n.z, u.y, d.y, zm.y, zp.y, rr.y, w0, wx, wy, wzm, wzp, adt);
+                        v.z = upd7(n.z, n.y, n.w, u.z, d.z, zm.z, zp.z, rr.z, w0, wx, wy, wzm, wzp, adt);
+                        v.w = upd7(n.w, n.z, r, u.w, d.w, zm.w, zp.w, rr.w, w0, wx, wy, wzm, wzp, adt);
+                        if (valid[it] && !failed) {
+                            *reinterpret_cast<float4 *>((s ? outm : outp) + off[it]) = v;
+                            if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
                             if (!PERIODIC) {
-                                if (c4 == 0) lx[s] += n.x;
-                                if (c4 == ncol4 - 1) lx[s] += n.w;
-                                if (yg == 0) ly[s] += nsum;
-                                if (yg == ny - 1) ly[s] += nsum;
+                                if (c4_[it] == 0) lat[s] += n.x;
+                                if (c4_[it] == ncol4 - 1) lat[s] += n.w;
+                                if (zero_u[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
+                                if (zero_d[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
                             }
                         }
                         prev[it][s] = n;
                         cur[it][s] = zp;
                     }
-                    if (ivalid[it]) rsum += (rr.x + rr.y) + (rr.z + rr.w);
+                    if (valid[it]) rsum += (rr.x + rr.y) + (rr.z + rr.w);
+                    off[it] += plane;
                 }
-                acc[0] += (double)rsum;
+                // FP32 partial sums over at most 32 planes, then FP64
+                if (++nacc == 32) { acc[0] += (double)rsum; rsum = 0.f; nacc = 0; }
                 if (k == 0) { acc[1] += (double)an[0]; acc[2] += (double)an[1]; }
-                if (k == nz - 1) { acc[3] += (double)ca[0]; acc[4] += (double)ca[1]; }
+                if (k == nz - 1) { acc[3] += (double)an[0]; acc[4] += (double)an[1]; }
                 if (!PERIODIC) {
-                    acc[5] += (double)lx[0] * cf.latx_f[0] + (double)ly[0] * cf.laty_f[0];
-                    acc[6] += (double)lx[1] * cf.latx_f[1] + (double)ly[1] * cf.laty_f[1];
+                    // lateral faces: x and y weights are equal for dx = dy (latx_f == laty_f)
+                    acc[5] += (double)lat[0] * cf.latx_f[0];
+                    acc[6] += (double)lat[1] * cf.latx_f[1];
                 }
+                release(pc);
+                if (has_next) { pc = pos; pos.advance(S); }
             }
-            if (__syncthreads_or(failed)) goto abort_path;
-            // slot of plane k is free: refill it with the next plane in order
-            if (issued_hi + 1 <= ze) {
-                if (tid == 0) {
-                    fence_proxy_async();
-                    issue(issued_hi + 1);
-                }
-                ++issued_hi;
-            }
+            acc[0] += (double)rsum;
+            if (zb < nz) release(pc);   // the z1 halo plane of this segment
+            if (failed) break;
         }
-        block_sum<7>(acc, red);
-        if (tid == 0) {
-            double *sl = slots + (size_t)blockIdx.x * NT;
-            sl[0] += acc[0] * cf.rec_f;
-            sl[1] += acc[1] * cf.anode_f[0];
-            sl[2] += acc[2] * cf.anode_f[1];
-            sl[3] += acc[3] * cf.cathode_f[0];
-            sl[4] += acc[4] * cf.cathode_f[1];
-            sl[5] += acc[5];
-            sl[6] += acc[6];
+        if (failed && lane == 0) {
+            abort_flag = 1;
+            atomicExch(err, 1);
         }
-        return;
     }
-
-abort_path:
-    if (tid == 0) {
-        atomicExch(err, 1);
-        // wait (bounded) for every plane still in flight before the CTA exits
-        for (int p = zs; p <= issued_hi; ++p) (void)mbar_wait_bounded(&bars[(p - zs) % zc.S], parity_of(p));
+    block_sum<7>(acc, red);
+    if (tid == 0 && !abort_flag) {
+        double *sl = slots + (size_t)blockIdx.x * NT;
+        sl[0] += acc[0] * cf.rec_f;
+        sl[1] += acc[1] * cf.anode_f[0];
+        sl[2] += acc[2] * cf.anode_f[1];
+        sl[3] += acc[3] * cf.cathode_f[0];
+        sl[4] += acc[4] * cf.cathode_f[1];
+        sl[5] += acc[5];
+        sl[6] += acc[6];
     }
-    __syncthreads();
 }
+
+}  // namespace itk
+
+namespace itk {
 
 // ---------------------------------------------------------------------------
 // host side: launch shape and tensor maps
@@ -392,10 +433,11 @@ static int zm_occupancy(size_t smem) {
     return n;
 }
 
-static int ipt_of(const it_ctx *c, int TY) { return ((c->g.nx / 4) * TY + ZM_THREADS - 1) / ZM_THREADS; }
+static int ipt_of(const it_ctx *c, int TY) { return ((c->g.nx / 4) * TY + ZM_CT - 1) / ZM_CT; }
 
-// Fill c->zm for a requested TY / nzc / S (0 = choose) and build the maps.
-int zmarch_setup(it_ctx *c, int want_ty, int want_nzc, int want_s) {
+// Fill c->zm for a requested tile height / CTAs per SM / ring depth
+// (0 = choose) and build the tensor maps.
+int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s) {
     const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
     if (c->prec != IT_FP32) { set_error("z-march kernel needs FP32 densities"); return IT_EINVAL; }
     if (nx % 4 != 0) { set_error("z-march kernel needs nx % 4 == 0"); return IT_EINVAL; }
@@ -404,8 +446,8 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_nzc, int want_s) {
     z.threads = ZM_THREADS;
     z.bx = nx <= 256 ? nx : 256;
     z.nbx = nx / z.bx;
-    // rows per tile: the smallest divisor of ny that gives every thread a
-    // float4 item, with at most ZM_MAX_IPT items per thread
+    // rows per tile: the smallest divisor of ny that gives every consumer
+    // thread a float4 item, with at most ZM_MAX_IPT items per thread
     int TY = want_ty;
     if (TY <= 0) {
         TY = 0;
@@ -413,7 +455,7 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_nzc, int want_s) {
             if (ny % t) continue;
             if (ipt_of(c, t) > ZM_MAX_IPT) break;
             TY = t;
-            if ((nx / 4) * t >= ZM_THREADS) break;
+            if ((nx / 4) * t >= ZM_CT) break;
         }
     }
     if (TY <= 0 || ny % TY != 0 || ipt_of(c, TY) > ZM_MAX_IPT || TY > 255) {
@@ -427,11 +469,13 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_nzc, int want_s) {
     z.reg_bot = z.reg_main + align32f(TY * z.bx);
     z.blk = z.reg_bot + align32f(z.bx);
     z.slot = 2 * z.nbx * z.blk;
-    z.S = want_s > 0 ? want_s : 4;
-    if (z.S < 3 || z.S > 8) { set_error("z-march ring depth must be 3..8"); return IT_EINVAL; }
+    const int cps = want_cps > 0 ? want_cps : 1;
+    const size_t budget = (size_t)(220 * 1024) / cps;
+    z.S = want_s > 0 ? want_s : 8;
+    if (z.S < 3 || z.S > 16) { set_error("z-march ring depth must be 3..16"); return IT_EINVAL; }
     for (;;) {
-        z.smem = (size_t)z.S * z.slot * sizeof(float) + 8 * 8 + 128;   // barriers + alignment slack
-        if (z.smem <= 200 * 1024 || z.S == 3) break;
+        z.smem = (size_t)z.S * z.slot * sizeof(float) + 16 * z.S + 128;   // ring + barriers + alignment slack
+        if (z.smem <= budget || z.S == 3 || want_s > 0) break;
         --z.S;
     }
     if (z.smem > 227 * 1024) { set_error("z-march kernel: tile does not fit in shared memory"); return IT_EINVAL; }
@@ -445,19 +489,13 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_nzc, int want_s) {
     ZM_CASE(false, 1) ZM_CASE(false, 2) ZM_CASE(false, 3) ZM_CASE(false, 4)
 #undef ZM_CASE
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(z-march)");
-    if (occ < 1) { set_error("z-march kernel: zero occupancy"); return IT_EINVAL; }
-    z.ctas_per_sm = occ;
+    if (occ < cps) { set_error("z-march kernel: requested CTAs per SM do not fit"); return IT_EINVAL; }
+    z.ctas_per_sm = cps;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nzc = want_nzc;
-    if (nzc <= 0) {
-        const int resident = sms * occ;
-        nzc = std::max(1, resident / z.ntile);
-        nzc = std::min(nzc, std::max(1, nz / 8));   // keep chunks at least ~8 planes deep
-    }
-    if (nzc > nz) nzc = nz;
-    z.nzc = nzc;
+    const long long tp = (long long)z.ntile * nz;
+    z.nzc = (int)std::min<long long>((long long)sms * cps, tp);   // grid: CTAs (each a contiguous range)
     for (int set = 0; set < 2; ++set)
         for (int s = 0; s < 2; ++s) {
             int rc = encode_map(&c->tm_main[set][s], c->n[set][s], nx, ny, nz, z.bx, TY);
@@ -466,7 +504,7 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_nzc, int want_s) {
             if (rc) return rc;
         }
     c->zm = z;
-    c->zm_grid = z.ntile * z.nzc;
+    c->zm_grid = z.nzc;
     return IT_OK;
 }
 

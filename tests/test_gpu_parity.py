@@ -29,8 +29,10 @@ def _lib():
     B.lib()
 
 
-def assert_density_close(gpu, orc, tol, core=5e-2, what=""):
-    scale = np.max(np.abs(orc))
+def assert_density_close(gpu, orc, tol, core=5e-2, what="", floor=0.0, ptol=None):
+    """floor: smallest scale the error is measured against (densities that
+    have almost all left the domain are compared with the released scale)."""
+    scale = max(np.max(np.abs(orc)), floor)
     if scale == 0:
         assert np.max(np.abs(gpu)) == 0
         return
@@ -39,10 +41,13 @@ def assert_density_close(gpu, orc, tol, core=5e-2, what=""):
     at = np.unravel_index(np.argmax(diff), diff.shape)
     assert err <= tol, f"{what}: max abs error / max = {err:.3e} > {tol} at {at}: {gpu[at]} vs {orc[at]}"
     big = np.abs(orc) >= core * scale
+    if not big.any():
+        return
+    ptol = tol if ptol is None else ptol
     rel = diff[big] / np.abs(orc[big])
     q = np.argmax(rel)
-    assert rel[q] <= tol, (f"{what}: pointwise relative error {rel[q]:.3e} > {tol} at "
-                           f"{tuple(np.argwhere(big)[q])}")
+    assert rel[q] <= ptol, (f"{what}: pointwise relative error {rel[q]:.3e} > {ptol} at "
+                            f"{tuple(np.argwhere(big)[q])}")
 
 
 def make_pair(nx, ny, nz, dx, V, tracks, precision=B.IT_FP32, lateral=B.IT_PERIODIC,
@@ -60,11 +65,12 @@ def make_pair(nx, ny, nz, dx, V, tracks, precision=B.IT_FP32, lateral=B.IT_PERIO
 
 
 def compare_tallies(tg, to, f_tol, rel_tol):
+    """Charges are compared relative to the released total (a species can be
+    almost entirely collected, leaving an in-domain residue near zero)."""
     assert tg.f == pytest.approx(to.f, abs=f_tol)
-    for name in ("released", "in_domain"):
-        np.testing.assert_allclose(getattr(tg, name), getattr(to, name), rtol=rel_tol)
+    np.testing.assert_allclose(tg.released, to.released, rtol=rel_tol)
     tot = to.released.sum()
-    for name in ("collected_anode", "collected_cathode", "lost_lateral"):
+    for name in ("in_domain", "collected_anode", "collected_cathode", "lost_lateral"):
         np.testing.assert_allclose(getattr(tg, name), getattr(to, name), rtol=0, atol=rel_tol * tot)
     assert tg.recombined == pytest.approx(to.recombined, abs=rel_tol * tot)
 
@@ -115,7 +121,7 @@ def test_fp64_storage_matches_oracle_to_rounding(lat):
         g.step(60)
         O.step(60)
         for s in range(2):
-            assert_density_close(g.density(s), O.density(s), 1e-12, core=1e-3)
+            assert_density_close(g.density(s), O.density(s), 1e-12, core=1e-3, ptol=1e-10)
         compare_tallies(g.tallies(), O.tallies(), 1e-12, 1e-12)
 
 
@@ -194,8 +200,9 @@ def test_degenerate_grids(shape):
         O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
         g.step(9)
         O.step(9)
+        floor = 1e-6 * O.tallies().released[0] / (nx * ny * nz * dx ** 3)
         for s in range(2):
-            assert_density_close(g.density(s), O.density(s), 1e-4)
+            assert_density_close(g.density(s), O.density(s), 1e-4, floor=floor)
         compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
 
 
