@@ -216,6 +216,23 @@ int it_device_state(it_ctx *ctx, void **plus, void **minus, void **stream);
  * (IT_ESTATE otherwise).  IT_EINVAL if the shape does not fit the grid. */
 int it_set_launch(it_ctx *ctx, int kernel, int tile_rows, int ctas_per_sm, int stages);
 
+/* As it_set_launch, plus the grid of the z-march kernel: 0 = one CTA per
+ * resident slot (SMs x ctas_per_sm); -1 = the largest multiple of the
+ * y-tile count that fits those slots (every tile column is then cut at the
+ * same z, so adjacent tiles are streamed in step); > 0 = that many CTAs. */
+int it_set_launch_ex(it_ctx *ctx, int kernel, int tile_rows, int ctas_per_sm, int stages, int grid);
+
+/* Time candidate launch shapes of the step kernel on the context's current
+ * densities and keep the fastest (a native autotuner).  Each candidate runs
+ * 2 untimed and trial_steps timed steps (rounded up to even, 8 if <= 0) on a
+ * copy of the state, which is restored afterwards: the densities, tallies
+ * and step counter are unchanged on return.  Only before the first step
+ * (IT_ESTATE otherwise).  The choice is cached per grid shape, precision and
+ * lateral boundary for the life of the process (flags & 1 forces a new
+ * search).  *best_us (may be NULL) receives the chosen shape's time per
+ * step in microseconds. */
+int it_autotune(it_ctx *ctx, int trial_steps, int flags, double *best_us);
+
 /* Report the kernel in use, its launch shape and its CTA count. */
 int it_get_launch(it_ctx *ctx, int *kernel, int *tile_rows, int *ctas_per_sm, int *stages, int *ctas);
 

@@ -88,6 +88,8 @@ def lib():
             "it_reset": (I, [P]),
             "it_device_state": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),
             "it_set_launch": (I, [P, I, I, I, I]),
+            "it_set_launch_ex": (I, [P, I, I, I, I, I]),
+            "it_autotune": (I, [P, I, I, DP]),
             "it_get_launch": (I, [P, IP, IP, IP, IP, IP]),
             "it_destroy": (I, [P]),
         }
@@ -225,6 +227,16 @@ def it_set_launch(h, kernel=IT_KERNEL_AUTO, tile_rows=0, ctas_per_sm=0, stages=0
     _check(lib().it_set_launch(h, int(kernel), int(tile_rows), int(ctas_per_sm), int(stages)))
 
 
+def it_set_launch_ex(h, kernel=IT_KERNEL_AUTO, tile_rows=0, ctas_per_sm=0, stages=0, grid=0):
+    _check(lib().it_set_launch_ex(h, int(kernel), int(tile_rows), int(ctas_per_sm), int(stages), int(grid)))
+
+
+def it_autotune(h, trial_steps=8, flags=0) -> float:
+    us = ctypes.c_double()
+    _check(lib().it_autotune(h, int(trial_steps), int(flags), ctypes.byref(us)))
+    return us.value
+
+
 def it_get_launch(h):
     v = [ctypes.c_int() for _ in range(5)]
     _check(lib().it_get_launch(h, *[ctypes.byref(x) for x in v]))
@@ -331,8 +343,14 @@ class Simulation:
     def launch(self):
         return it_get_launch(self.h)
 
-    def set_launch(self, kernel=IT_KERNEL_AUTO, tile_rows=0, ctas_per_sm=0, stages=0):
-        it_set_launch(self.h, kernel, tile_rows, ctas_per_sm, stages)
+    def set_launch(self, kernel=IT_KERNEL_AUTO, tile_rows=0, ctas_per_sm=0, stages=0, grid=0):
+        it_set_launch_ex(self.h, kernel, tile_rows, ctas_per_sm, stages, grid)
+
+    def autotune(self, trial_steps=8, force=False) -> float:
+        """Pick the fastest step-kernel launch shape on the current state
+        (which is left unchanged); returns its time per step in us (-1 if
+        the shape came from the per-process cache)."""
+        return it_autotune(self.h, trial_steps, 1 if force else 0)
 
     def close(self):
         if getattr(self, "h", None):

@@ -240,6 +240,35 @@ static int run_plain(it_ctx *c, int64_t n) {
     return IT_OK;
 }
 
+// Reconfigure the step kernel (no step-count check); tally slots restart.
+int set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages, int grid) {
+    if (kernel == IT_KERNEL_SIMPLE) {
+        c->kernel = IT_KERNEL_SIMPLE;
+    } else if (kernel == IT_KERNEL_ZMARCH || kernel == IT_KERNEL_AUTO) {
+        int rc = zmarch_setup(c, tile_rows, ctas_per_sm, stages, grid);
+        if (rc) {
+            if (kernel == IT_KERNEL_ZMARCH) return rc;
+            c->kernel = IT_KERNEL_SIMPLE;
+        } else {
+            c->kernel = IT_KERNEL_ZMARCH;
+        }
+    } else {
+        return fail(IT_EINVAL, "bad kernel");
+    }
+    const int n = c->kernel == IT_KERNEL_ZMARCH ? c->zm_grid : simple_grid(c);
+    if (n != c->nslots) {
+        double *ns = nullptr;
+        IT_CK(cudaMalloc(&ns, sizeof(double) * NT * n));
+        IT_CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_slots);
+        c->d_slots = ns;
+        c->nslots = n;
+    }
+    IT_CK(cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream));
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return IT_OK;
+}
+
 }  // namespace itk
 
 using namespace itk;
@@ -581,34 +610,14 @@ int it_device_state(it_ctx *c, void **plus, void **minus, void **stream) {
     return IT_OK;
 }
 
-int it_set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages) {
+int it_set_launch_ex(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages, int grid) {
     if (!c) return fail(IT_EINVAL, "ctx is NULL");
     if (c->steps != 0) return fail(IT_ESTATE, "launch shape can only change before the first step");
-    if (kernel == IT_KERNEL_SIMPLE) {
-        c->kernel = IT_KERNEL_SIMPLE;
-    } else if (kernel == IT_KERNEL_ZMARCH || kernel == IT_KERNEL_AUTO) {
-        int rc = zmarch_setup(c, tile_rows, ctas_per_sm, stages);
-        if (rc) {
-            if (kernel == IT_KERNEL_ZMARCH) return rc;
-            c->kernel = IT_KERNEL_SIMPLE;
-        } else {
-            c->kernel = IT_KERNEL_ZMARCH;
-        }
-    } else {
-        return fail(IT_EINVAL, "bad kernel");
-    }
-    const int n = c->kernel == IT_KERNEL_ZMARCH ? c->zm_grid : simple_grid(c);
-    if (n != c->nslots) {
-        double *ns = nullptr;
-        IT_CK(cudaMalloc(&ns, sizeof(double) * NT * n));
-        cudaStreamSynchronize(c->stream);
-        cudaFree(c->d_slots);
-        c->d_slots = ns;
-        c->nslots = n;
-    }
-    IT_CK(cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream));
-    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-    return IT_OK;
+    return set_launch(c, kernel, tile_rows, ctas_per_sm, stages, grid);
+}
+
+int it_set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages) {
+    return it_set_launch_ex(c, kernel, tile_rows, ctas_per_sm, stages, 0);
 }
 
 int it_get_launch(it_ctx *c, int *kernel, int *tile_rows, int *ctas_per_sm, int *stages, int *ctas) {

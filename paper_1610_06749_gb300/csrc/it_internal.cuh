@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/iontracks.h"
+#include "iontracks.h"
 
 namespace itk {
 
@@ -137,7 +137,8 @@ int cuda_fail(cudaError_t e, const char *what);
 int launch_step_simple(it_ctx *c, cudaStream_t s);
 int launch_step_zmarch(it_ctx *c, cudaStream_t s);
 int zmarch_configure(it_ctx *c);
-int zmarch_setup(it_ctx *c, int want_ty, int want_nzc, int want_s);
+int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid);
+int set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages, int grid);
 int launch_finalize(it_ctx *c, cudaStream_t s);
 int launch_monitor(it_ctx *c, cudaStream_t s);
 int launch_deposit(it_ctx *c, int64_t n, cudaStream_t s);   // tracks already in d_tracks

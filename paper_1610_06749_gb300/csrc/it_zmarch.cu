@@ -87,13 +87,24 @@ struct ZmMaps {
     CUtensorMap halo[2];
 };
 
-constexpr int ZM_NCW = 16;                       // consumer warps
-constexpr int ZM_CT = ZM_NCW * 32;               // consumer threads
-constexpr int ZM_THREADS = ZM_CT + 32;           // + one producer warp
-constexpr int ZM_MAX_IPT = 4;                    // float4 items per consumer thread
+constexpr int ZM_MAX_IPT = 4;                    // float4 items per thread
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
 // Position in the ring: slot index and the parity of its current phase.
@@ -105,21 +116,50 @@ struct RingPos {
     }
 };
 
-// Warp-specialised persistent step kernel.
-//   warp ZM_NCW (producer): lane 0 streams the planes this CTA needs into an
-//     S-deep ring with TMA; full[slot] completes when a plane's bytes land,
-//     empty[slot] when all consumer warps have released it.
-//   warps 0..ZM_NCW-1 (consumers): march up z, one plane per iteration,
-//     without block-wide barriers.
-// Work: the tile-planes (y-tile t, plane z) in the order t*nz + z are split
-// into gridDim.x equal contiguous ranges, one per CTA; a range may cover the
-// end of one tile column and the start of the next (each such segment loads
-// its own z-1 / z1 halo planes).
-template <bool PERIODIC, int IPT>
-__global__ void __launch_bounds__(ZM_THREADS, 1)
+// The CTA's work: tile-planes (y-tile t, plane z) in the order t*nz + z,
+// split into gridDim.x equal contiguous ranges.  A range is walked as
+// segments (one tile column each); a segment computing planes [za, zb) loads
+// planes max(za-1,0) .. min(zb, nz-1).
+struct Segs {
+    long long L, g1;
+    int nz;
+    int t, za, zb;
+    __device__ __forceinline__ bool next() {
+        if (L >= g1) return false;
+        t = (int)(L / nz);
+        za = (int)(L - (long long)t * nz);
+        zb = (int)min((long long)nz, za + (g1 - L));
+        L += zb - za;
+        return true;
+    }
+    __device__ __forceinline__ int lo() const { return za > 0 ? za - 1 : 0; }
+    __device__ __forceinline__ int hi() const { return zb < nz ? zb : nz - 1; }
+};
+
+// Producer state (lane 0 of warp 0): walks the same segments as the
+// consumers and issues one plane per ring slot.
+struct Producer {
+    Segs seg;
+    int p;            // next plane of the current segment to issue
+    bool live;        // a plane remains to be issued
+    RingPos pos;
+    uint32_t issued;
+};
+
+// Warp-specialised-by-lane persistent step kernel (NW warps, all consumers).
+//   Lane 0 of warp 0 also streams the planes this CTA needs into an S-deep
+//   ring with TMA ("pump", non-blocking): full[slot] completes when a plane's
+//   bytes land, empty[slot] when all NW warps have released it.  Warp 0 keeps
+//   pumping while it waits for data, so a plane is always issued before
+//   anyone needs it.
+//   Every warp marches up z, one plane per iteration, with no block-wide
+//   barrier inside the march.
+template <bool PERIODIC, int IPT, int NW>
+__global__ void __launch_bounds__(NW * 32, (NW <= 8 ? 2 : 1))
 step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp, float *__restrict__ outm,
                    int nx, int ny, int nz, const ZmConf zc, const Coef<float> cf, double *__restrict__ slots,
                    int *__restrict__ err) {
+    constexpr int NT_ = NW * 32;
     extern __shared__ __align__(128) unsigned char zm_smem_raw[];
     // TMA destinations need 128-byte alignment: round the base up explicitly
     unsigned char *smem_base = zm_smem_raw + ((128u - (smem_u32(zm_smem_raw) & 127u)) & 127u);
@@ -142,227 +182,229 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
             mbar_init(&full[q], 1);
-            mbar_init(&empty[q], ZM_NCW);
+            mbar_init(&empty[q], NW);
         }
         abort_flag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
+    const bool is_producer = tid == 0;
+    Producer pr;
+    if (is_producer) {
+        pr.seg = Segs{g0, g1, nz, 0, 0, 0};
+        pr.live = pr.seg.next();
+        pr.p = pr.live ? pr.seg.lo() : 0;
+        pr.pos = RingPos{0, 0u};
+        pr.issued = 0;
+    }
+    // issue as many planes as free slots allow (lane 0 of warp 0 only)
+    auto pump = [&]() {
+        while (pr.live) {
+            if (pr.issued >= (uint32_t)S && !mbar_test_wait(&empty[pr.pos.slot], pr.pos.phase ^ 1u)) return;
+            const int y0 = pr.seg.t * zc.TY;
+            const bool has_top = PERIODIC || y0 > 0;
+            const bool has_bot = PERIODIC || y0 + zc.TY < ny;
+            const int ytop = y0 > 0 ? y0 - 1 : ny - 1;
+            const int ybot = y0 + zc.TY < ny ? y0 + zc.TY : 0;
+            const uint32_t tx = 2u * zc.nbx * (uint32_t)(zc.TY + has_top + has_bot) * zc.bx * 4u;
+            float *base = ring + (size_t)pr.pos.slot * zc.slot;
+            uint64_t *bar = &full[pr.pos.slot];
+            fence_proxy_async();
+            mbar_arrive_expect_tx(bar, tx);
+            for (int s = 0; s < 2; ++s) {
+                for (int b = 0; b < zc.nbx; ++b) {
+                    float *blk = base + (size_t)(s * zc.nbx + b) * zc.blk;
+                    tma_load3(blk + zc.reg_main, &maps.main[s], bar, b * zc.bx, y0, pr.p);
+                    if (has_top) tma_load3(blk + zc.reg_top, &maps.halo[s], bar, b * zc.bx, ytop, pr.p);
+                    if (has_bot) tma_load3(blk + zc.reg_bot, &maps.halo[s], bar, b * zc.bx, ybot, pr.p);
+                }
+            }
+            ++pr.issued;
+            pr.pos.advance(S);
+            if (++pr.p > pr.seg.hi()) {
+                pr.live = pr.seg.next();
+                if (pr.live) pr.p = pr.seg.lo();
+            }
+        }
+    };
+
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
 
-    if (warp == ZM_NCW) {
-        // ------------------------------------------------------------ producer
-        if (lane == 0) {
-            RingPos pos{0, 0u};
-            uint32_t issued = 0;
-            bool ok = true;
-            for (long long L = g0; L < g1 && ok;) {
-                const int t = (int)(L / nz), za = (int)(L % nz);
-                const int zb = (int)min((long long)nz, za + (g1 - L));
-                L += zb - za;
-                const int y0 = t * zc.TY;
-                const bool has_top = PERIODIC || y0 > 0;
-                const bool has_bot = PERIODIC || y0 + zc.TY < ny;
-                const int ytop = y0 > 0 ? y0 - 1 : ny - 1;
-                const int ybot = y0 + zc.TY < ny ? y0 + zc.TY : 0;
-                const uint32_t tx = 2u * zc.nbx * (uint32_t)(zc.TY + has_top + has_bot) * zc.bx * 4u;
-                const int lo = za > 0 ? za - 1 : 0, hi = zb < nz ? zb : nz - 1;
-                for (int p = lo; p <= hi; ++p) {
-                    // reuse of a slot waits until all consumers released its previous plane
-                    if (issued >= (uint32_t)S) {
-                        if (abort_flag || !mbar_wait_bounded(&empty[pos.slot], pos.phase ^ 1u)) {
-                            ok = false;
-                            break;
-                        }
-                    }
-                    float *base = ring + (size_t)pos.slot * zc.slot;
-                    mbar_arrive_expect_tx(&full[pos.slot], tx);
-                    for (int s = 0; s < 2; ++s) {
-                        for (int b = 0; b < zc.nbx; ++b) {
-                            float *blk = base + (size_t)(s * zc.nbx + b) * zc.blk;
-                            tma_load3(blk + zc.reg_main, &maps.main[s], &full[pos.slot], b * zc.bx, y0, p);
-                            if (has_top)
-                                tma_load3(blk + zc.reg_top, &maps.halo[s], &full[pos.slot], b * zc.bx, ytop, p);
-                            if (has_bot)
-                                tma_load3(blk + zc.reg_bot, &maps.halo[s], &full[pos.slot], b * zc.bx, ybot, p);
-                        }
-                    }
-                    ++issued;
-                    pos.advance(S);
-                }
-            }
-            if (!ok) {
-                abort_flag = 1;
-                atomicExch(err, 1);
-                // every issued load must land before the CTA may exit: wait
-                // (bounded) for the last phase issued on each slot
-                for (int j = 0; j < S; ++j) {
-                    if ((uint32_t)j >= issued) break;
-                    const uint32_t ph = j < pos.slot ? pos.phase : (pos.phase ^ 1u);
-                    (void)mbar_wait_bounded(&full[j], ph);
-                }
+    // per-item offsets inside a species block (species 1: + nbx*blk)
+    int o_c[IPT], o_u[IPT], o_d[IPT], o_l[IPT], o_r[IPT], ty_[IPT], c4_[IPT];
+    bool valid[IPT], need_l[IPT], need_r[IPT], zero_l[IPT], zero_r[IPT];
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+        const int q = tid + it * NT_;
+        valid[it] = q < nitems;
+        const int qe = valid[it] ? q : nitems - 1;
+        const int ty = qe / ncol4, c4 = qe - (qe / ncol4) * ncol4;
+        ty_[it] = ty;
+        c4_[it] = c4;
+        const int x0 = 4 * c4;
+        const int xb = x0 / zc.bx, xi = x0 - xb * zc.bx;
+        const int bofs = xb * zc.blk;
+        o_c[it] = bofs + zc.reg_main + ty * zc.bx + xi;
+        o_u[it] = bofs + (ty == 0 ? zc.reg_top : zc.reg_main + (ty - 1) * zc.bx) + xi;
+        o_d[it] = bofs + (ty == zc.TY - 1 ? zc.reg_bot : zc.reg_main + (ty + 1) * zc.bx) + xi;
+        // x neighbours come by shuffle from the adjacent lane, except where
+        // that lane is outside the warp or the row: then one scalar is read
+        // from shared memory (wrapped at a periodic row end, zero at an
+        // absorbing one)
+        const bool row_start = c4 == 0, row_end = c4 == ncol4 - 1;
+        need_l[it] = lane == 0 || row_start;
+        need_r[it] = lane == 31 || row_end;
+        zero_l[it] = !PERIODIC && row_start;
+        zero_r[it] = !PERIODIC && row_end;
+        const int xl = row_start ? nx - 1 : x0 - 1;
+        const int xr = row_end ? 0 : x0 + 4;
+        o_l[it] = (xl / zc.bx) * zc.blk + zc.reg_main + ty * zc.bx + (xl % zc.bx);
+        o_r[it] = (xr / zc.bx) * zc.blk + zc.reg_main + ty * zc.bx + (xr % zc.bx);
+    }
+    const int sp_ofs = zc.nbx * zc.blk;
+    const size_t plane = (size_t)nx * ny;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    RingPos pos{0, 0u};
+    bool failed = false;
+
+    // Wait for the plane at ring position u.  Warp 0 pumps while it waits.
+    // A lost wait (about 2^32 cycles) marks the whole warp failed, so
+    // shuffles stay convergent.
+    auto wait_full = [&](const RingPos &u) {
+        if (warp == 0 && is_producer) pump();
+        bool ok = failed ? false : mbar_test_wait(&full[u.slot], u.phase);
+        if (!__all_sync(0xffffffffu, ok) && !failed) {
+            const long long t0 = clock64();
+            for (;;) {
+                if (is_producer) pump();
+                ok = ok || mbar_try_wait(&full[u.slot], u.phase);
+                if (__all_sync(0xffffffffu, ok)) break;
+                if (abort_flag || clock64() - t0 > (1LL << 32)) { ok = false; break; }
             }
         }
-    } else {
-        // ------------------------------------------------------------ consumers
-        const int ct = tid;                       // 0 .. ZM_CT-1
-        // per-item offsets inside a species block (species 1: + nbx*blk)
-        int o_c[IPT], o_u[IPT], o_d[IPT], o_l[IPT], o_r[IPT], ty_[IPT], c4_[IPT];
-        bool valid[IPT], need_l[IPT], need_r[IPT], zero_l[IPT], zero_r[IPT];
+        failed = __any_sync(0xffffffffu, !ok);
+    };
+    auto release = [&](const RingPos &u) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[u.slot]);
+    };
+
+    Segs seg{g0, g1, nz, 0, 0, 0};
+    while (seg.next()) {
+        const int za = seg.za, zb = seg.zb;
+        const int y0 = seg.t * zc.TY;
+        float4 prev[IPT][2], cur[IPT][2];
+        size_t off[IPT];
+        bool zero_u[IPT], zero_d[IPT];
 #pragma unroll
         for (int it = 0; it < IPT; ++it) {
-            const int q = ct + it * ZM_CT;
-            valid[it] = q < nitems;
-            const int qe = valid[it] ? q : nitems - 1;
-            const int ty = qe / ncol4, c4 = qe - (qe / ncol4) * ncol4;
-            ty_[it] = ty;
-            c4_[it] = c4;
-            const int x0 = 4 * c4;
-            const int xb = x0 / zc.bx, xi = x0 - xb * zc.bx;
-            const int bofs = xb * zc.blk;
-            o_c[it] = bofs + zc.reg_main + ty * zc.bx + xi;
-            o_u[it] = bofs + (ty == 0 ? zc.reg_top : zc.reg_main + (ty - 1) * zc.bx) + xi;
-            o_d[it] = bofs + (ty == zc.TY - 1 ? zc.reg_bot : zc.reg_main + (ty + 1) * zc.bx) + xi;
-            // x neighbours come by shuffle from the adjacent lane, except where
-            // that lane is outside the warp or the row: then one scalar is read
-            // from shared memory (wrapped at a periodic row end, zero at an
-            // absorbing one)
-            const bool row_start = c4 == 0, row_end = c4 == ncol4 - 1;
-            need_l[it] = lane == 0 || row_start;
-            need_r[it] = lane == 31 || row_end;
-            zero_l[it] = !PERIODIC && row_start;
-            zero_r[it] = !PERIODIC && row_end;
-            const int xl = row_start ? nx - 1 : x0 - 1;
-            const int xr = row_end ? 0 : x0 + 4;
-            o_l[it] = (xl / zc.bx) * zc.blk + zc.reg_main + ty * zc.bx + (xl % zc.bx);
-            o_r[it] = (xr / zc.bx) * zc.blk + zc.reg_main + ty * zc.bx + (xr % zc.bx);
+            const int yg = y0 + ty_[it];
+            off[it] = ((size_t)za * ny + yg) * nx + 4 * c4_[it];
+            zero_u[it] = !PERIODIC && yg == 0;
+            zero_d[it] = !PERIODIC && yg == ny - 1;
         }
-        const int sp_ofs = zc.nbx * zc.blk;
-        const size_t plane = (size_t)nx * ny;
-        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        RingPos pos{0, 0u};
-        bool failed = false;
-
-        // a lost wait marks the whole warp failed, so shuffles stay convergent
-        auto wait_full = [&](const RingPos &u) {
-            const bool bad = failed || abort_flag || !mbar_wait_bounded(&full[u.slot], u.phase);
-            failed = __any_sync(0xffffffffu, bad);
-        };
-        auto release = [&](const RingPos &u) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[u.slot]);
-        };
-
-        for (long long L = g0; L < g1;) {
-            const int t = (int)(L / nz), za = (int)(L % nz);
-            const int zb = (int)min((long long)nz, za + (g1 - L));
-            L += zb - za;
-            const int y0 = t * zc.TY;
-            float4 prev[IPT][2], cur[IPT][2];
-            size_t off[IPT];
-            bool zero_u[IPT], zero_d[IPT], lat_y[IPT];
+        if (za > 0) {
+            wait_full(pos);
+            const float *sl = ring + (size_t)pos.slot * zc.slot;
 #pragma unroll
             for (int it = 0; it < IPT; ++it) {
-                const int yg = y0 + ty_[it];
-                off[it] = ((size_t)za * ny + yg) * nx + 4 * c4_[it];
-                zero_u[it] = !PERIODIC && yg == 0;
-                zero_d[it] = !PERIODIC && yg == ny - 1;
-                lat_y[it] = zero_u[it] || zero_d[it];
+                prev[it][0] = *reinterpret_cast<const float4 *>(sl + o_c[it]);
+                prev[it][1] = *reinterpret_cast<const float4 *>(sl + sp_ofs + o_c[it]);
             }
-            if (za > 0) {
-                wait_full(pos);
-                const float *sl = ring + (size_t)pos.slot * zc.slot;
-#pragma unroll
-                for (int it = 0; it < IPT; ++it) {
-                    prev[it][0] = *reinterpret_cast<const float4 *>(sl + o_c[it]);
-                    prev[it][1] = *reinterpret_cast<const float4 *>(sl + sp_ofs + o_c[it]);
-                }
-                release(pos);
-                pos.advance(S);
-            } else {
-#pragma unroll
-                for (int it = 0; it < IPT; ++it) prev[it][0] = prev[it][1] = zero4;
-            }
-            wait_full(pos);
-            RingPos pc = pos;
+            release(pos);
             pos.advance(S);
-            {
-                const float *sl = ring + (size_t)pc.slot * zc.slot;
+        } else {
 #pragma unroll
-                for (int it = 0; it < IPT; ++it) {
-                    cur[it][0] = *reinterpret_cast<const float4 *>(sl + o_c[it]);
-                    cur[it][1] = *reinterpret_cast<const float4 *>(sl + sp_ofs + o_c[it]);
-                }
-            }
-            float rsum = 0.f;
-            int nacc = 0;
-            for (int k = za; k < zb; ++k) {
-                const bool has_next = k + 1 < nz;
-                if (has_next) wait_full(pos);
-                const float *sk = ring + (size_t)pc.slot * zc.slot;
-                const float *sn = ring + (size_t)pos.slot * zc.slot;
-                float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
-#pragma unroll
-                for (int it = 0; it < IPT; ++it) {
-                    const float4 P = cur[it][0], M = cur[it][1];
-                    const float4 rr = make_float4(P.x * M.x, P.y * M.y, P.z * M.z, P.w * M.w);
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const float *bk = sk + s * sp_ofs;
-                        const float4 n = cur[it][s];
-                        float4 u = *reinterpret_cast<const float4 *>(bk + o_u[it]);
-                        float4 d = *reinterpret_cast<const float4 *>(bk + o_d[it]);
-                        const float4 zp = has_next ? *reinterpret_cast<const float4 *>(sn + s * sp_ofs + o_c[it]) : zero4;
-                        if (zero_u[it]) u = zero4;
-                        if (zero_d[it]) d = zero4;
-                        float l = __shfl_up_sync(0xffffffffu, n.w, 1);
-                        float r = __shfl_down_sync(0xffffffffu, n.x, 1);
-                        if (need_l[it]) l = zero_l[it] ? 0.f : bk[o_l[it]];
-                        if (need_r[it]) r = zero_r[it] ? 0.f : bk[o_r[it]];
-                        const float4 zm = prev[it][s];
-                        const float w0 = cf.w0[s], wx = cf.wx[s], wy = cf.wy[s], wzm = cf.wzm[s], wzp = cf.wzp[s];
-                        const float adt = cf.adt;
-                        float4 v;
-                        v.x = upd7(n.x, l, n.y, u.x, d.x, zm.x, zp.x, rr.x, w0, wx, wy, wzm, wzp, adt);
-                        v.y = upd7(n.y, n.x, n.z, u.y, d.y, zm.y, zp.y, rr.y, w0, wx, wy, wzm, wzp, adt);
-                        v.z = upd7(n.z, n.y, n.w, u.z, d.z, zm.z, zp.z, rr.z, w0, wx, wy, wzm, wzp, adt);
-                        v.w = upd7(n.w, n.z, r, u.w, d.w, zm.w, zp.w, rr.w, w0, wx, wy, wzm, wzp, adt);
-                        if (valid[it] && !failed) {
-                            *reinterpret_cast<float4 *>((s ? outm : outp) + off[it]) = v;
-                            if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
-                            if (!PERIODIC) {
-                                if (c4_[it] == 0) lat[s] += n.x;
-                                if (c4_[it] == ncol4 - 1) lat[s] += n.w;
-                                if (zero_u[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
-                                if (zero_d[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
-                            }
-                        }
-                        prev[it][s] = n;
-                        cur[it][s] = zp;
-                    }
-                    if (valid[it]) rsum += (rr.x + rr.y) + (rr.z + rr.w);
-                    off[it] += plane;
-                }
-                // FP32 partial sums over at most 32 planes, then FP64
-                if (++nacc == 32) { acc[0] += (double)rsum; rsum = 0.f; nacc = 0; }
-                if (k == 0) { acc[1] += (double)an[0]; acc[2] += (double)an[1]; }
-                if (k == nz - 1) { acc[3] += (double)an[0]; acc[4] += (double)an[1]; }
-                if (!PERIODIC) {
-                    // lateral faces: x and y weights are equal for dx = dy (latx_f == laty_f)
-                    acc[5] += (double)lat[0] * cf.latx_f[0];
-                    acc[6] += (double)lat[1] * cf.latx_f[1];
-                }
-                release(pc);
-                if (has_next) { pc = pos; pos.advance(S); }
-            }
-            acc[0] += (double)rsum;
-            if (zb < nz) release(pc);   // the z1 halo plane of this segment
-            if (failed) break;
+            for (int it = 0; it < IPT; ++it) prev[it][0] = prev[it][1] = zero4;
         }
-        if (failed && lane == 0) {
-            abort_flag = 1;
-            atomicExch(err, 1);
+        wait_full(pos);
+        RingPos pc = pos;
+        pos.advance(S);
+        {
+            const float *sl = ring + (size_t)pc.slot * zc.slot;
+#pragma unroll
+            for (int it = 0; it < IPT; ++it) {
+                cur[it][0] = *reinterpret_cast<const float4 *>(sl + o_c[it]);
+                cur[it][1] = *reinterpret_cast<const float4 *>(sl + sp_ofs + o_c[it]);
+            }
+        }
+        float rsum = 0.f;
+        int nacc = 0;
+        for (int k = za; k < zb; ++k) {
+            const bool has_next = k + 1 < nz;
+            if (has_next) wait_full(pos);
+            const float *sk = ring + (size_t)pc.slot * zc.slot;
+            const float *sn = ring + (size_t)pos.slot * zc.slot;
+            float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
+#pragma unroll
+            for (int it = 0; it < IPT; ++it) {
+                const float4 P = cur[it][0], M = cur[it][1];
+                const float4 rr = make_float4(P.x * M.x, P.y * M.y, P.z * M.z, P.w * M.w);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const float *bk = sk + s * sp_ofs;
+                    const float4 n = cur[it][s];
+                    float4 u = *reinterpret_cast<const float4 *>(bk + o_u[it]);
+                    float4 d = *reinterpret_cast<const float4 *>(bk + o_d[it]);
+                    const float4 zp = has_next ? *reinterpret_cast<const float4 *>(sn + s * sp_ofs + o_c[it]) : zero4;
+                    if (zero_u[it]) u = zero4;
+                    if (zero_d[it]) d = zero4;
+                    float l = __shfl_up_sync(0xffffffffu, n.w, 1);
+                    float r = __shfl_down_sync(0xffffffffu, n.x, 1);
+                    if (need_l[it]) l = zero_l[it] ? 0.f : bk[o_l[it]];
+                    if (need_r[it]) r = zero_r[it] ? 0.f : bk[o_r[it]];
+                    const float4 zm = prev[it][s];
+                    const float w0 = cf.w0[s], wx = cf.wx[s], wy = cf.wy[s], wzm = cf.wzm[s], wzp = cf.wzp[s];
+                    const float adt = cf.adt;
+                    float4 v;
+                    v.x = upd7(n.x, l, n.y, u.x, d.x, zm.x, zp.x, rr.x, w0, wx, wy, wzm, wzp, adt);
+                    v.y = upd7(n.y, n.x, n.z, u.y, d.y, zm.y, zp.y, rr.y, w0, wx, wy, wzm, wzp, adt);
+                    v.z = upd7(n.z, n.y, n.w, u.z, d.z, zm.z, zp.z, rr.z, w0, wx, wy, wzm, wzp, adt);
+                    v.w = upd7(n.w, n.z, r, u.w, d.w, zm.w, zp.w, rr.w, w0, wx, wy, wzm, wzp, adt);
+                    if (valid[it] && !failed) {
+                        *reinterpret_cast<float4 *>((s ? outm : outp) + off[it]) = v;
+                        if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
+                        if (!PERIODIC) {
+                            if (c4_[it] == 0) lat[s] += n.x;
+                            if (c4_[it] == ncol4 - 1) lat[s] += n.w;
+                            if (zero_u[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
+                            if (zero_d[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
+                        }
+                    }
+                    prev[it][s] = n;
+                    cur[it][s] = zp;
+                }
+                if (valid[it]) rsum += (rr.x + rr.y) + (rr.z + rr.w);
+                off[it] += plane;
+            }
+            // FP32 partial sums over at most 32 planes, then FP64
+            if (++nacc == 32) { acc[0] += (double)rsum; rsum = 0.f; nacc = 0; }
+            if (k == 0) { acc[1] += (double)an[0]; acc[2] += (double)an[1]; }
+            if (k == nz - 1) { acc[3] += (double)an[0]; acc[4] += (double)an[1]; }
+            if (!PERIODIC) {
+                // lateral faces: x and y weights are equal for dx = dy (latx_f == laty_f)
+                acc[5] += (double)lat[0] * cf.latx_f[0];
+                acc[6] += (double)lat[1] * cf.latx_f[1];
+            }
+            release(pc);
+            if (has_next) { pc = pos; pos.advance(S); }
+        }
+        acc[0] += (double)rsum;
+        if (zb < nz) release(pc);   // the z1 halo plane of this segment
+        if (failed) break;
+    }
+    if (failed && lane == 0) {
+        abort_flag = 1;
+        atomicExch(err, 1);
+    }
+    if (is_producer && (failed || abort_flag)) {
+        // every issued load must land before the CTA may exit: wait (bounded)
+        // for the last phase issued on each slot
+        for (int j = 0; j < S; ++j) {
+            if ((uint32_t)j >= pr.issued) break;
+            const uint32_t ph = j < pr.pos.slot ? pr.pos.phase : (pr.pos.phase ^ 1u);
+            (void)mbar_wait_bounded(&full[j], ph);
         }
     }
     block_sum<7>(acc, red);
@@ -420,45 +462,49 @@ static int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx
 
 static int align32f(int floats) { return (floats + 31) / 32 * 32; }   // 128-byte multiple of floats
 
-template <bool P, int I>
+template <bool P, int I, int W>
 static cudaError_t zm_set_attr(size_t smem) {
-    return cudaFuncSetAttribute(step_zmarch_kernel<P, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(step_zmarch_kernel<P, I, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <bool P, int I>
+template <bool P, int I, int W>
 static int zm_occupancy(size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_zmarch_kernel<P, I>, ZM_THREADS, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_zmarch_kernel<P, I, W>, W * 32, smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-static int ipt_of(const it_ctx *c, int TY) { return ((c->g.nx / 4) * TY + ZM_CT - 1) / ZM_CT; }
+static int ipt_of(const it_ctx *c, int TY, int nw) { return ((c->g.nx / 4) * TY + nw * 32 - 1) / (nw * 32); }
 
 // Fill c->zm for a requested tile height / CTAs per SM / ring depth
-// (0 = choose) and build the tensor maps.
-int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s) {
+// (0 = choose) and build the tensor maps.  One CTA per SM runs 16 warps,
+// two CTAs per SM run 8 warps each.
+int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid) {
     const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
     if (c->prec != IT_FP32) { set_error("z-march kernel needs FP32 densities"); return IT_EINVAL; }
     if (nx % 4 != 0) { set_error("z-march kernel needs nx % 4 == 0"); return IT_EINVAL; }
     if (nx > 256 && nx % 256 != 0) { set_error("z-march kernel needs nx <= 256 or nx % 256 == 0"); return IT_EINVAL; }
+    const int cps = want_cps > 0 ? want_cps : 1;
+    if (cps > 2) { set_error("z-march kernel runs 1 or 2 CTAs per SM"); return IT_EINVAL; }
+    const int nw = cps == 1 ? 16 : 8;
     ZmConf z{};
-    z.threads = ZM_THREADS;
+    z.threads = nw * 32;
     z.bx = nx <= 256 ? nx : 256;
     z.nbx = nx / z.bx;
-    // rows per tile: the smallest divisor of ny that gives every consumer
-    // thread a float4 item, with at most ZM_MAX_IPT items per thread
+    // rows per tile: the smallest divisor of ny that gives every thread two
+    // float4 items (else the largest with at most ZM_MAX_IPT)
     int TY = want_ty;
     if (TY <= 0) {
         TY = 0;
         for (int t = 1; t <= ny; ++t) {
             if (ny % t) continue;
-            if (ipt_of(c, t) > ZM_MAX_IPT) break;
+            if (ipt_of(c, t, nw) > ZM_MAX_IPT) break;
             TY = t;
-            if ((nx / 4) * t >= ZM_CT) break;
+            if ((nx / 4) * t >= 2 * z.threads) break;
         }
     }
-    if (TY <= 0 || ny % TY != 0 || ipt_of(c, TY) > ZM_MAX_IPT || TY > 255) {
+    if (TY <= 0 || ny % TY != 0 || ipt_of(c, TY, nw) > ZM_MAX_IPT || TY > 255) {
         set_error("z-march kernel: no usable tile height for this grid");
         return IT_EINVAL;
     }
@@ -469,7 +515,6 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s) {
     z.reg_bot = z.reg_main + align32f(TY * z.bx);
     z.blk = z.reg_bot + align32f(z.bx);
     z.slot = 2 * z.nbx * z.blk;
-    const int cps = want_cps > 0 ? want_cps : 1;
     const size_t budget = (size_t)(220 * 1024) / cps;
     z.S = want_s > 0 ? want_s : 8;
     if (z.S < 3 || z.S > 16) { set_error("z-march ring depth must be 3..16"); return IT_EINVAL; }
@@ -480,13 +525,15 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s) {
     }
     if (z.smem > 227 * 1024) { set_error("z-march kernel: tile does not fit in shared memory"); return IT_EINVAL; }
     const bool per = c->p.lateral_bc == IT_PERIODIC;
-    const int ipt = ipt_of(c, TY);
+    const int ipt = ipt_of(c, TY, nw);
     cudaError_t e = cudaSuccess;
     int occ = 0;
-#define ZM_CASE(P, I) \
-    if (per == P && ipt == I) { e = zm_set_attr<P, I>(z.smem); occ = zm_occupancy<P, I>(z.smem); }
-    ZM_CASE(true, 1) ZM_CASE(true, 2) ZM_CASE(true, 3) ZM_CASE(true, 4)
-    ZM_CASE(false, 1) ZM_CASE(false, 2) ZM_CASE(false, 3) ZM_CASE(false, 4)
+#define ZM_CASE(P, I, W) \
+    if (per == P && ipt == I && nw == W) { e = zm_set_attr<P, I, W>(z.smem); occ = zm_occupancy<P, I, W>(z.smem); }
+    ZM_CASE(true, 1, 16) ZM_CASE(true, 2, 16) ZM_CASE(true, 3, 16) ZM_CASE(true, 4, 16)
+    ZM_CASE(false, 1, 16) ZM_CASE(false, 2, 16) ZM_CASE(false, 3, 16) ZM_CASE(false, 4, 16)
+    ZM_CASE(true, 1, 8) ZM_CASE(true, 2, 8) ZM_CASE(true, 3, 8) ZM_CASE(true, 4, 8)
+    ZM_CASE(false, 1, 8) ZM_CASE(false, 2, 8) ZM_CASE(false, 3, 8) ZM_CASE(false, 4, 8)
 #undef ZM_CASE
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(z-march)");
     if (occ < cps) { set_error("z-march kernel: requested CTAs per SM do not fit"); return IT_EINVAL; }
@@ -494,8 +541,16 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // grid: CTAs, each taking one contiguous range of tile-planes.  0: one
+    // per resident slot; -1: the largest multiple of the tile count that
+    // fits the resident slots, so every tile column is cut at the same z and
+    // vertically adjacent tiles are streamed in step (their halo rows are
+    // then still in L2); > 0: as given.
     const long long tp = (long long)z.ntile * nz;
-    z.nzc = (int)std::min<long long>((long long)sms * cps, tp);   // grid: CTAs (each a contiguous range)
+    long long grid = (long long)sms * cps;
+    if (want_grid == -1 && grid >= z.ntile) grid = grid / z.ntile * z.ntile;
+    else if (want_grid > 0) grid = want_grid;
+    z.nzc = (int)std::min<long long>(grid, tp);
     for (int set = 0; set < 2; ++set)
         for (int s = 0; s < 2; ++s) {
             int rc = encode_map(&c->tm_main[set][s], c->n[set][s], nx, ny, nz, z.bx, TY);
@@ -508,7 +563,7 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s) {
     return IT_OK;
 }
 
-int zmarch_configure(it_ctx *c) { return zmarch_setup(c, 0, 0, 0); }
+int zmarch_configure(it_ctx *c) { return zmarch_setup(c, 0, 0, 0, 0); }
 
 int launch_step_zmarch(it_ctx *c, cudaStream_t s) {
     const int cur = c->cur, nxt = cur ^ 1;
@@ -520,14 +575,17 @@ int launch_step_zmarch(it_ctx *c, cudaStream_t s) {
     float *op = (float *)c->n[nxt][0], *om = (float *)c->n[nxt][1];
     const ZmConf &z = c->zm;
     const bool per = c->p.lateral_bc == IT_PERIODIC;
-    const int ipt = ipt_of(c, z.TY);
+    const int nw = z.threads / 32;
+    const int ipt = ipt_of(c, z.TY, nw);
     const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
-#define ZM_LAUNCH(P, I)                                                                                 \
-    if (per == P && ipt == I)                                                                           \
-        step_zmarch_kernel<P, I><<<c->zm_grid, ZM_THREADS, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, \
-                                                                        c->d_slots, c->d_err);
-    ZM_LAUNCH(true, 1) ZM_LAUNCH(true, 2) ZM_LAUNCH(true, 3) ZM_LAUNCH(true, 4)
-    ZM_LAUNCH(false, 1) ZM_LAUNCH(false, 2) ZM_LAUNCH(false, 3) ZM_LAUNCH(false, 4)
+#define ZM_LAUNCH(P, I, W)                                                                            \
+    if (per == P && ipt == I && nw == W)                                                              \
+        step_zmarch_kernel<P, I, W><<<c->zm_grid, W * 32, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, \
+                                                                       c->d_slots, c->d_err);
+    ZM_LAUNCH(true, 1, 16) ZM_LAUNCH(true, 2, 16) ZM_LAUNCH(true, 3, 16) ZM_LAUNCH(true, 4, 16)
+    ZM_LAUNCH(false, 1, 16) ZM_LAUNCH(false, 2, 16) ZM_LAUNCH(false, 3, 16) ZM_LAUNCH(false, 4, 16)
+    ZM_LAUNCH(true, 1, 8) ZM_LAUNCH(true, 2, 8) ZM_LAUNCH(true, 3, 8) ZM_LAUNCH(true, 4, 8)
+    ZM_LAUNCH(false, 1, 8) ZM_LAUNCH(false, 2, 8) ZM_LAUNCH(false, 3, 8) ZM_LAUNCH(false, 4, 8)
 #undef ZM_LAUNCH
     IT_CK(cudaGetLastError());
     c->cur = nxt;
