@@ -215,7 +215,12 @@ def run_ours(args, ws, rank, local):
     xy_host = np.ascontiguousarray(np.stack([tracks.x_cm, tracks.y_cm], axis=1))
     torch.cuda.synchronize()          # d_tracks was written on torch's default stream
     B.it_deposit_tracks_device(sim.h, ntr, d_tracks.data_ptr())
-    tune_us = sim.autotune(trial_steps=8)
+    if args.launch:
+        ty, cps, st, grid = (int(v) for v in args.launch.split(","))
+        sim.set_launch(B.IT_KERNEL_ZMARCH, ty, cps, st, grid)
+        tune_us = None
+    else:
+        tune_us = sim.autotune(trial_steps=8)
     sim.reset()
     launch = sim.launch()
     cells, seg = w.cells, args.seg
@@ -336,6 +341,7 @@ def main():
     ap.add_argument("--voltage", type=float, default=200.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default="", help="fixed z-march shape TY,ctas_per_sm,stages,grid (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
