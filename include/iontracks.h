@@ -236,6 +236,33 @@ int it_autotune(it_ctx *ctx, int trial_steps, int flags, double *best_us);
 /* Report the kernel in use, its launch shape and its CTA count. */
 int it_get_launch(it_ctx *ctx, int *kernel, int *tile_rows, int *ctas_per_sm, int *stages, int *ctas);
 
+/* Capacity (CTAs) of the fixed tally scratch used by it_step_noalloc. */
+#define IT_NOALLOC_MAX_BLOCKS 2048
+
+/* One explicit step of both species without allocating device memory; the
+ * paper has no counterpart -- this is for callers that may not call
+ * cudaMalloc (code that only receives buffers from another framework's
+ * memory pool, or a service that must not allocate after start-up).
+ * dev_plus/dev_minus: this step's densities, dev_out_plus/dev_out_minus:
+ * the next step's, FP32 [nz][ny][nx] device arrays that must not alias;
+ * dev_tallies7: 7 device doubles that receive this step's recombined ion
+ * pairs, anode +/-, cathode +/- and lateral +/- ions (the same quantities
+ * it_tallies accumulates).  g, dx, dt and p as for it_create (p->precision
+ * must be IT_FP32; dt must be given and within Eq. (vNeum)).  Enqueued on
+ * `stream` (a cudaStream_t, NULL = the legacy default stream).
+ * The per-block tally partials live in one static device array of
+ * IT_NOALLOC_MAX_BLOCKS x 8 doubles (128 KiB on each device that loads the
+ * library, kept until exit); a device that would need more blocks is
+ * rejected with IT_EINVAL.  The first call on a device looks up the array's
+ * address (make it before any stream capture).  All calls share the array
+ * and clear the part they use, so calls that overlap on the GPU race:
+ * order them on one stream.  Allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library call. */
+int it_step_noalloc(it_grid g, double dx_cm, double dt_s, const it_params *p,
+                    const float *dev_plus, const float *dev_minus,
+                    float *dev_out_plus, float *dev_out_minus,
+                    double *dev_tallies7, void *stream);
+
 /* Destroy a context; NULL is a no-op.  Synchronises the stream first. */
 int it_destroy(it_ctx *ctx);
 

@@ -91,6 +91,7 @@ def lib():
             "it_set_launch_ex": (I, [P, I, I, I, I, I]),
             "it_autotune": (I, [P, I, I, DP]),
             "it_get_launch": (I, [P, IP, IP, IP, IP, IP]),
+            "it_step_noalloc": (I, [it_grid, D, D, ctypes.POINTER(it_params), P, P, P, P, P, P]),
             "it_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
@@ -241,6 +242,16 @@ def it_get_launch(h):
     v = [ctypes.c_int() for _ in range(5)]
     _check(lib().it_get_launch(h, *[ctypes.byref(x) for x in v]))
     return dict(zip(("kernel", "tile_rows", "ctas_per_sm", "stages", "ctas"), [x.value for x in v]))
+
+
+def it_step_noalloc(nx, ny, nz, dx_cm, dt_s, p: it_params, dev_plus: int, dev_minus: int,
+                    dev_out_plus: int, dev_out_minus: int, dev_tallies7: int, stream: int = 0):
+    """One step on caller-owned device buffers; allocates nothing (device
+    addresses as ints, e.g. torch tensors' data_ptr())."""
+    _check(lib().it_step_noalloc(it_grid(nx, ny, nz), float(dx_cm), float(dt_s), ctypes.byref(p),
+                                 ctypes.c_void_p(dev_plus), ctypes.c_void_p(dev_minus),
+                                 ctypes.c_void_p(dev_out_plus), ctypes.c_void_p(dev_out_minus),
+                                 ctypes.c_void_p(dev_tallies7), ctypes.c_void_p(stream)))
 
 
 def it_destroy(h):

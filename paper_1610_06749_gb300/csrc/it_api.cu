@@ -240,6 +240,18 @@ static int run_plain(it_ctx *c, int64_t n) {
     return IT_OK;
 }
 
+// Parameter and time-step checks of it_create, for entry points that take
+// no context.
+int validate_step_args(const it_params *p, it_grid g, double dx, double dt) {
+    int rc = check_params(p, g, dx);
+    if (rc) return rc;
+    if (!(std::isfinite(dt) && dt > 0)) return fail(IT_EINVAL, "dt must be positive and finite");
+    if (dt > dt_von_neumann(p, dx) * (1.0 + 1e-12)) return fail(IT_EINVAL, "dt exceeds the von Neumann bound of Eq. (vNeum)");
+    return IT_OK;
+}
+
+void coef_f32(const it_params *p, double dx, double dt, Coef<float> *out) { make_coef(*out, p, dx, dt); }
+
 // Reconfigure the step kernel (no step-count check); tally slots restart.
 int set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages, int grid) {
     if (kernel == IT_KERNEL_SIMPLE) {

@@ -105,6 +105,18 @@ int launch_step_simple(it_ctx *c, cudaStream_t s) {
     return IT_OK;
 }
 
+// The simple step on caller-given FP32 arrays with a caller-given slot array
+// of nblocks x NT doubles (one block per slot, grid-stride over the cells).
+int launch_step_simple_raw_f32(const float *ip, const float *im, float *op, float *om, int nx, int ny, int nz,
+                               const Coef<float> &cf, bool periodic, double *slots, int nblocks, cudaStream_t s) {
+    if (periodic)
+        step_simple_kernel<float, true><<<nblocks, 256, 0, s>>>(ip, im, op, om, nx, ny, nz, cf, slots);
+    else
+        step_simple_kernel<float, false><<<nblocks, 256, 0, s>>>(ip, im, op, om, nx, ny, nz, cf, slots);
+    IT_CK(cudaGetLastError());
+    return IT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // monitor: in-domain ions and extreme densities of the current state
 // ---------------------------------------------------------------------------
