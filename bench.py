@@ -152,6 +152,68 @@ def cpu_oracle_rate(w, tracks, seconds):
     return w.cells * n / el / 1e9, int(os.environ.get("OMP_NUM_THREADS", cores)), n, el
 
 
+def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=None):
+    """Solves/s of the 256-simulation batch (uneven grids 32^3 .. 128x128x200,
+    one launch per step for all running simulations, CUDA-graph segments)
+    against the plain one-context-per-simulation solver on the same GPU.
+    The plain solver runs a subset (the first n_subset simulations); the batch
+    is timed on that subset too, and on all 256.  Context creation is outside
+    the timed regions; deposition and the run to completion are inside.
+    Runs to completion use the upwind drift: at the recombination-bound time
+    step the Courant number is small and Lax-Wendroff's undershoots make the
+    explicit recombination term a source (it diverges, in the FP64 oracle
+    too), while upwind stays positive."""
+    import torch
+    if scheme is None:
+        scheme = B.IT_UPWIND
+    descs = synth.batch_descriptors()
+    tracks = [synth.batch_tracks(d) for d in descs]
+    sims = []
+    for d, tr in zip(descs, tracks):
+        sims.append(dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], dx_cm=d["dx_cm"], voltage_V=d["voltage_V"],
+                         n_peak_cm3=B.it_peak_density(tr.let_keV_um, tr.b_cm)))
+
+    def run_batch(idx):
+        bt = B.Batch([sims[q] for q in idx], scheme=scheme)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, q in enumerate(idx):
+            tr = tracks[q]
+            bt.deposit(k, tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        bt.retime()                      # dt bound from each deposited peak (overlaps included)
+        launches = bt.run(tol=tol, check_every=check_every)
+        el = time.perf_counter() - t0
+        out = [bt.tallies(k) for k in range(len(idx))]
+        bt.close()
+        return el, out, launches
+
+    t_all, tal_all, launches = run_batch(list(range(len(sims))))
+    sub = list(range(n_subset))
+    t_bsub, tal_bsub, _ = run_batch(sub)
+    ctxs = [B.Simulation(sims[q]["nx"], sims[q]["ny"], sims[q]["nz"], sims[q]["dx_cm"], sims[q]["voltage_V"],
+                         n_peak_cm3=sims[q]["n_peak_cm3"], scheme=scheme) for q in sub]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f_plain = []
+    for q, g in zip(sub, ctxs):
+        tr = tracks[q]
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        g.retime()
+        g.run_to_completion(tol=tol, check_every=check_every)
+        f_plain.append(g.tallies().f)
+    t_plain = time.perf_counter() - t0
+    for g in ctxs:
+        g.close()
+    df = max(abs(a.f - b) for a, b in zip(tal_bsub, f_plain))
+    cell_updates = sum(sims[q]["nx"] * sims[q]["ny"] * sims[q]["nz"] * tal_all[q].steps for q in range(len(sims)))
+    return {"sims": len(sims), "solves_per_s": len(sims) / t_all, "seconds": t_all, "step_launches": launches,
+            "Gcell_updates_per_s": cell_updates / t_all / 1e9,
+            "subset": n_subset, "subset_batched_solves_per_s": n_subset / t_bsub,
+            "subset_plain_solves_per_s": n_subset / t_plain,
+            "speedup_vs_plain": (n_subset / t_bsub) / (n_subset / t_plain),
+            "max_abs_df_vs_plain": df, "df_bound": 1e-3, "scheme": "upwind" if scheme == B.IT_UPWIND else "lax-wendroff"}
+
+
 def run_reference(args, ws, rank):
     from paper_1610_06749_gb300 import synth
     import oracle.oracle as o
@@ -294,6 +356,10 @@ def run_ours(args, ws, rank, local):
     achieved = BYTES_PER_CELL_UPDATE * cells / t_kernel / 1e9
     traffic = ncu_traffic()
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_vs_plain(B, synth)
+
     line = None
     if rank == 0:
         cpu = None
@@ -322,6 +388,7 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": args.steps * (seg + 4),   # per step: 4 deposit kernels + seg step kernels
             "clocks": clocks,
             "f_last": t.f,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -341,6 +408,7 @@ def main():
     ap.add_argument("--voltage", type=float, default=200.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain solves/s measurement")
     ap.add_argument("--launch", default="", help="fixed z-march shape TY,ctas_per_sm,stages,grid (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:

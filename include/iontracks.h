@@ -201,6 +201,13 @@ int it_get_density(it_ctx *ctx, int species, void *host_dst, size_t bytes);
  * becomes the FP64 sum of what was set, the step counter returns to 0. */
 int it_set_density(it_ctx *ctx, const void *plus, const void *minus, size_t bytes);
 
+/* Set the time step before the first step (IT_ESTATE otherwise).  dt_s > 0
+ * is checked against Eq. (vNeum); dt_s <= 0 applies it_auto_dt with n_peak
+ * taken as the largest density of the current state (the deposited pulse,
+ * overlaps of tracks included).  The recombination bound then holds for the
+ * state actually deposited. */
+int it_retime(it_ctx *ctx, double dt_s);
+
 /* Return the context to its freshly created state without reallocating:
  * densities zero, all tallies zero, step counter 0, schedule cleared.
  * Asynchronous on the context stream (no host synchronisation). */
@@ -235,6 +242,57 @@ int it_autotune(it_ctx *ctx, int trial_steps, int flags, double *best_us);
 
 /* Report the kernel in use, its launch shape and its CTA count. */
 int it_get_launch(it_ctx *ctx, int *kernel, int *tile_rows, int *ctas_per_sm, int *stages, int *ctas);
+
+/* ---------------------------------------------------------------------------
+ * Batched simulations: many independent simulations of uneven grids, each
+ * with its own dx, voltage and time step, advanced together -- one launch
+ * per step covers every simulation still running, and segments of launches
+ * are replayed from a CUDA graph.  Each simulation computes exactly what a
+ * single context with the same parameters computes (bitwise-identical
+ * densities).
+ * ------------------------------------------------------------------------- */
+typedef struct it_batch it_batch;
+
+typedef struct {
+    int32_t nx, ny, nz;     /* cells; gap = nz * dx */
+    double dx_cm;
+    double dt_s;            /* <= 0: it_auto_dt with this simulation's voltage and n_peak */
+    double voltage_V;
+    double n_peak_cm3;      /* peak density for the recombination dt bound (0: none) */
+} it_sim_desc;
+
+/* Create nsim simulations.  common supplies mu, D, alpha, W, lateral_bc,
+ * scheme, cfl_safety and react_kappa (its gap, voltage and n_peak are
+ * ignored); precision must be IT_FP32.  Errors as for it_create, with the
+ * offending simulation's index in the message. */
+int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *common, it_batch **out);
+
+/* Deposit n tracks into simulation `sim` (arrays as in it_deposit_tracks);
+ * only before the first step (IT_ESTATE otherwise).  Synchronous. */
+int it_batch_deposit_tracks(it_batch *b, int32_t sim, int64_t n, const double *xy_cm,
+                            const double *let_keV_um, const double *b_cm);
+
+/* After the deposits and before the first step: every simulation created
+ * with dt_s <= 0 gets it_auto_dt with n_peak = the largest density of its
+ * deposited state (IT_ESTATE after the first step). */
+int it_batch_retime(it_batch *b);
+
+/* Cells per work-table entry (one CTA each; default 16384). */
+int it_batch_set_chunk(it_batch *b, int64_t cells_per_block);
+
+/* Run every simulation until its in-domain charge / released < tol or it
+ * has taken max_steps steps, checked every check_every steps (rounded up to
+ * even).  *launches (may be NULL) receives the number of step launches. */
+int it_batch_run(it_batch *b, double tol, int64_t max_steps, int64_t check_every, int64_t *launches);
+
+/* Tallies of one simulation (FP64; as it_tallies). */
+int it_batch_tallies(it_batch *b, int32_t sim, it_tallies_t *out);
+
+/* Densities of one simulation to host memory (FP32, [nz][ny][nx]). */
+int it_batch_get_density(it_batch *b, int32_t sim, int species, void *host_dst, size_t bytes);
+
+/* Free a batch; NULL is a no-op. */
+int it_batch_destroy(it_batch *b);
 
 /* Capacity (CTAs) of the fixed tally scratch used by it_step_noalloc. */
 #define IT_NOALLOC_MAX_BLOCKS 2048

@@ -53,6 +53,12 @@ class it_tallies_t(ctypes.Structure):
                 ("n_min", ctypes.c_double * 2), ("n_max", ctypes.c_double * 2)]
 
 
+class it_sim_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx_cm", ctypes.c_double), ("dt_s", ctypes.c_double), ("voltage_V", ctypes.c_double),
+                ("n_peak_cm3", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -86,12 +92,22 @@ def lib():
             "it_get_density": (I, [P, I, P, SZ]),
             "it_set_density": (I, [P, P, P, SZ]),
             "it_reset": (I, [P]),
+            "it_retime": (I, [P, D]),
+            "it_batch_retime": (I, [P]),
             "it_device_state": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),
             "it_set_launch": (I, [P, I, I, I, I]),
             "it_set_launch_ex": (I, [P, I, I, I, I, I]),
             "it_autotune": (I, [P, I, I, DP]),
             "it_get_launch": (I, [P, IP, IP, IP, IP, IP]),
             "it_step_noalloc": (I, [it_grid, D, D, ctypes.POINTER(it_params), P, P, P, P, P, P]),
+            "it_batch_create": (I, [ctypes.c_int32, ctypes.POINTER(it_sim_desc), ctypes.POINTER(it_params),
+                                    ctypes.POINTER(P)]),
+            "it_batch_deposit_tracks": (I, [P, ctypes.c_int32, I64, DP, DP, DP]),
+            "it_batch_set_chunk": (I, [P, I64]),
+            "it_batch_run": (I, [P, D, I64, I64, I64P]),
+            "it_batch_tallies": (I, [P, ctypes.c_int32, ctypes.POINTER(it_tallies_t)]),
+            "it_batch_get_density": (I, [P, ctypes.c_int32, I, P, SZ]),
+            "it_batch_destroy": (I, [P]),
             "it_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
@@ -214,6 +230,14 @@ def it_set_density(h, plus: np.ndarray, minus: np.ndarray):
                                 plus.nbytes))
 
 
+def it_retime(h, dt_s=0.0):
+    _check(lib().it_retime(h, float(dt_s)))
+
+
+def it_batch_retime(h):
+    _check(lib().it_batch_retime(h))
+
+
 def it_reset(h):
     _check(lib().it_reset(h))
 
@@ -259,6 +283,44 @@ def it_destroy(h):
         _check(lib().it_destroy(h))
 
 
+def it_batch_create(descs, p: it_params):
+    arr = (it_sim_desc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _check(lib().it_batch_create(len(descs), arr, ctypes.byref(p), ctypes.byref(h)))
+    return h
+
+
+def it_batch_deposit_tracks(h, sim, xy_cm, let_keV_um, b_cm):
+    xy, L, b = _f64(xy_cm).reshape(-1), _f64(let_keV_um), _f64(b_cm)
+    _check(lib().it_batch_deposit_tracks(h, int(sim), L.size, _dp(xy), _dp(L), _dp(b)))
+
+
+def it_batch_set_chunk(h, cells_per_block):
+    _check(lib().it_batch_set_chunk(h, int(cells_per_block)))
+
+
+def it_batch_run(h, tol=1e-6, max_steps=10_000_000, check_every=64) -> int:
+    n = ctypes.c_int64()
+    _check(lib().it_batch_run(h, float(tol), int(max_steps), int(check_every), ctypes.byref(n)))
+    return n.value
+
+
+def it_batch_tallies(h, sim) -> it_tallies_t:
+    t = it_tallies_t()
+    _check(lib().it_batch_tallies(h, int(sim), ctypes.byref(t)))
+    return t
+
+
+def it_batch_get_density(h, sim, species, out: np.ndarray):
+    _check(lib().it_batch_get_density(h, int(sim), int(species), out.ctypes.data_as(ctypes.c_void_p), out.nbytes))
+    return out
+
+
+def it_batch_destroy(h):
+    if h:
+        _check(lib().it_batch_destroy(h))
+
+
 # --------------------------------------------------------------------------
 # convenience wrapper
 # --------------------------------------------------------------------------
@@ -287,6 +349,58 @@ class Tallies:
         a = lambda x: np.array([x[0], x[1]])
         return cls(a(t.released), a(t.collected_anode), a(t.collected_cathode), a(t.lost_lateral),
                    a(t.in_domain), t.recombined, t.f, t.t_s, t.dt_s, t.steps, a(t.n_min), a(t.n_max))
+
+
+class Batch:
+    """Many simulations advanced together (see it_batch_create)."""
+
+    def __init__(self, descs, mu=(1.73, 1.87), D=(0.037, 0.037), alpha=1.6e-6, W_eV=34.0,
+                 lateral_bc=IT_PERIODIC, scheme=IT_LAX_WENDROFF, cfl_safety=1.0, react_kappa=0.5):
+        self.descs = [it_sim_desc(int(d["nx"]), int(d["ny"]), int(d["nz"]), float(d["dx_cm"]),
+                                  float(d.get("dt_s", 0.0)), float(d["voltage_V"]), float(d.get("n_peak_cm3", 0.0)))
+                      for d in descs]
+        p = it_params_default(mu=mu, D=D, alpha=alpha, W_eV=W_eV, lateral_bc=lateral_bc, scheme=scheme,
+                              cfl_safety=cfl_safety, react_kappa=react_kappa, gap_cm=1.0)
+        self.h = it_batch_create(self.descs, p)
+
+    def deposit(self, sim, x_cm, y_cm, let_keV_um, b_cm):
+        xy = np.stack([np.asarray(x_cm, np.float64), np.asarray(y_cm, np.float64)], axis=1)
+        it_batch_deposit_tracks(self.h, sim, xy, let_keV_um, b_cm)
+
+    def retime(self):
+        """dt of every automatic-dt simulation from its deposited peak density."""
+        it_batch_retime(self.h)
+
+    def set_chunk(self, cells):
+        it_batch_set_chunk(self.h, cells)
+
+    def run(self, tol=1e-6, max_steps=10_000_000, check_every=64):
+        return it_batch_run(self.h, tol, max_steps, check_every)
+
+    def tallies(self, sim) -> "Tallies":
+        return Tallies.from_c(it_batch_tallies(self.h, sim))
+
+    def density(self, sim, species):
+        d = self.descs[sim]
+        out = np.empty((d.nz, d.ny, d.nx), dtype=np.float32)
+        return it_batch_get_density(self.h, sim, species, out)
+
+    def close(self):
+        if getattr(self, "h", None):
+            it_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Simulation:
@@ -350,6 +464,11 @@ class Simulation:
 
     def reset(self):
         it_reset(self.h)
+
+    def retime(self, dt_s=0.0):
+        """Before the first step: dt_s > 0 sets it; 0 derives it from the
+        largest density of the current (deposited) state."""
+        it_retime(self.h, dt_s)
 
     def launch(self):
         return it_get_launch(self.h)

@@ -602,6 +602,31 @@ int it_set_density(it_ctx *c, const void *plus, const void *minus, size_t bytes)
     return IT_OK;
 }
 
+int it_retime(it_ctx *c, double dt_s) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (c->steps != 0) return fail(IT_ESTATE, "the time step can only change before the first step");
+    it_params p = c->p;
+    double dt = dt_s;
+    if (!(dt_s > 0)) {
+        it_tallies_t t;
+        int rc = it_tallies(c, &t);
+        if (rc) return rc;
+        const double npk = std::max(t.n_max[0], t.n_max[1]);
+        if (!std::isfinite(npk)) return fail(IT_EUNSTABLE, "state is not finite");
+        p.n_peak_cm3 = npk > 0 ? npk : 0.0;
+        rc = it_auto_dt(&p, c->dx, &dt);
+        if (rc) return rc;
+    } else if (!std::isfinite(dt_s) || dt_s > dt_von_neumann(&p, c->dx) * (1.0 + 1e-12)) {
+        return fail(IT_EINVAL, "dt exceeds the von Neumann bound of Eq. (vNeum)");
+    }
+    c->p = p;
+    c->dt = dt;
+    make_coef(c->cf, &c->p, c->dx, dt);
+    make_coef(c->cd, &c->p, c->dx, dt);
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return IT_OK;
+}
+
 int it_reset(it_ctx *c) {
     if (!c) return fail(IT_EINVAL, "ctx is NULL");
     const size_t bytes = c->g.cells() * c->esize;

@@ -1,0 +1,814 @@
+// it_batch.cu -- many independent simulations advanced by one launch per step.
+//
+// Each simulation is the same method as a single context (Eq. theEquation
+// discretised as in the Appendix, deposition of Eqs. linear_density /
+// Gaussian / created, electrode tallies and f of Eq. collection_efficiency)
+// on its own grid, dx, voltage and time step.  All simulations live in four
+// shared FP32 arrays (two ping-pong sets of n+ and n-), each simulation
+// aligned to 256 bytes.  A work table lists (simulation, row range) entries;
+// one launch of step_batched_kernel advances every active simulation by one
+// of its own steps, and segments of launches are replayed from a CUDA graph.
+// At segment ends the per-entry tally slots are folded into per-simulation
+// FP64 accumulators in a fixed order, in-domain charge is measured, and
+// finished simulations leave the table.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "it_device.cuh"
+#include "it_internal.cuh"
+
+namespace itk {
+
+struct BatchSim {
+    int nx, ny, nz, pad;
+    long long off;          // element offset of this simulation in each state array
+    Coef<float> cf;
+};
+
+struct BatchEntry {
+    int sim, pad;
+    long long begin, end;   // row range inside the simulation (row = k * ny + j)
+};
+
+// One explicit step of the rows [begin, end) of one simulation; the same
+// per-cell operation sequence as the single-simulation kernels.  Thread t
+// owns x = t mod nx of every (256 / nx)-th row, so there is no division per
+// cell.
+template <bool PERIODIC>
+__global__ void __launch_bounds__(256)
+step_batched_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restrict__ tab,
+                    const float *__restrict__ ip_all, const float *__restrict__ im_all, float *__restrict__ op_all,
+                    float *__restrict__ om_all, double *__restrict__ slots) {
+    __shared__ double red[32 * 7];
+    __shared__ BatchSim S;
+    __shared__ BatchEntry E;
+    if (threadIdx.x == 0) {
+        E = tab[blockIdx.x];
+        S = sims[E.sim];
+    }
+    __syncthreads();
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const Coef<float> &c = S.cf;
+    const float *ip = ip_all + S.off, *im = im_all + S.off;
+    float *op = op_all + S.off, *om = om_all + S.off;
+    const int plane = nx * ny;
+    const int R = nx <= (int)blockDim.x ? (int)blockDim.x / nx : 1;   // rows per pass
+    const int lane_row = nx <= (int)blockDim.x ? (int)threadIdx.x / nx : 0;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (lane_row < R) {
+        const int i0 = nx <= (int)blockDim.x ? (int)threadIdx.x - lane_row * nx : (int)threadIdx.x;
+        long long row = E.begin + lane_row;
+        int k = (int)(row / ny), j = (int)(row - (long long)k * ny);
+        for (; row < E.end; row += R) {
+            for (int i = i0; i < nx; i += (nx <= (int)blockDim.x ? nx : (int)blockDim.x)) {
+                const int idx = (k * ny + j) * nx + i;
+                const int ixm = (i > 0) ? idx - 1 : idx + (nx - 1);
+                const int ixp = (i < nx - 1) ? idx + 1 : idx - (nx - 1);
+                const int iym = (j > 0) ? idx - nx : idx + (ny - 1) * nx;
+                const int iyp = (j < ny - 1) ? idx + nx : idx - (ny - 1) * nx;
+                const float p0 = ip[idx], m0 = im[idx];
+                const float rr = p0 * m0;
+                acc[0] += (double)rr;
+                const int cx = (i == 0) + (i == nx - 1);
+                const int cy = (j == 0) + (j == ny - 1);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const float *in = s ? im : ip;
+                    const float n0 = s ? m0 : p0;
+                    const float xm = (PERIODIC || i > 0) ? in[ixm] : 0.f;
+                    const float xp = (PERIODIC || i < nx - 1) ? in[ixp] : 0.f;
+                    const float ym = (PERIODIC || j > 0) ? in[iym] : 0.f;
+                    const float yp = (PERIODIC || j < ny - 1) ? in[iyp] : 0.f;
+                    const float zm = (k > 0) ? in[idx - plane] : 0.f;
+                    const float zp = (k < nz - 1) ? in[idx + plane] : 0.f;
+                    const float v =
+                        upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.w0[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
+                    (s ? om : op)[idx] = v;
+                    if (k == 0) acc[1 + s] += (double)n0;
+                    if (k == nz - 1) acc[3 + s] += (double)n0;
+                    if (!PERIODIC && (cx | cy)) acc[5 + s] += (double)n0 * (cx * c.latx_f[s] + cy * c.laty_f[s]);
+                }
+            }
+            j += R;
+            while (j >= ny) { j -= ny; ++k; }
+        }
+    }
+    block_sum<7>(acc, red);
+    if (threadIdx.x == 0) {
+        double *sl = slots + (size_t)blockIdx.x * NT;
+        sl[0] += acc[0] * c.rec_f;
+        sl[1] += acc[1] * c.anode_f[0];
+        sl[2] += acc[2] * c.anode_f[1];
+        sl[3] += acc[3] * c.cathode_f[0];
+        sl[4] += acc[4] * c.cathode_f[1];
+        sl[5] += acc[5];
+        sl[6] += acc[6];
+    }
+}
+
+// Entry of the float4 kernel: rows [y0, y0 + rows) of one simulation,
+// planes [z0, z1).
+struct VecEntry {
+    int sim, y0, rows, z0, z1, pad;
+};
+
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+// Float4 z-march for simulations with nx % 4 == 0: thread t owns x-segment
+// 4 (t mod nx/4) of row t div (nx/4), keeps planes k-1, k, k+1 of it in
+// registers, reads the y-neighbour rows with 16-byte loads (mostly L1/L2
+// hits: they are other threads' centres), and takes x-neighbours by warp
+// shuffle.  Same per-cell operation sequence as every other kernel.
+template <bool PERIODIC>
+__global__ void __launch_bounds__(256)
+step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__restrict__ tab,
+                        const float *__restrict__ ip_all, const float *__restrict__ im_all,
+                        float *__restrict__ op_all, float *__restrict__ om_all, double *__restrict__ slots) {
+    __shared__ double red[32 * 7];
+    __shared__ BatchSim S;
+    __shared__ VecEntry E;
+    if (threadIdx.x == 0) {
+        E = tab[blockIdx.x];
+        S = sims[E.sim];
+    }
+    __syncthreads();
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const Coef<float> &c = S.cf;
+    const float *in_[2] = {ip_all + S.off, im_all + S.off};
+    float *out_[2] = {op_all + S.off, om_all + S.off};
+    const int plane = nx * ny;
+    const int ncol4 = nx >> 2;
+    const int t = threadIdx.x, lane = t & 31;
+    const int ty = t / ncol4, c4 = t - (t / ncol4) * ncol4;
+    const bool valid = ty < E.rows;
+    const int yg = E.y0 + (valid ? ty : E.rows - 1);
+    const int x0 = 4 * c4;
+    const int row = yg * nx + x0;
+    const bool edge_u = yg == 0, edge_d = yg == ny - 1;
+    const int row_u = (edge_u ? ny - 1 : yg - 1) * nx + x0;
+    const int row_d = (edge_d ? 0 : yg + 1) * nx + x0;
+    const bool zero_u = !PERIODIC && edge_u, zero_d = !PERIODIC && edge_d;
+    const bool need_l = lane == 0 || c4 == 0, need_r = lane == 31 || c4 == ncol4 - 1;
+    const int row_l = yg * nx + (c4 == 0 ? nx - 1 : x0 - 1);
+    const int row_r = yg * nx + (c4 == ncol4 - 1 ? 0 : x0 + 4);
+    const bool zero_l = !PERIODIC && c4 == 0, zero_r = !PERIODIC && c4 == ncol4 - 1;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 prev[2], cur[2];
+    for (int s = 0; s < 2; ++s) {
+        prev[s] = E.z0 > 0 ? ldg4(in_[s] + (E.z0 - 1) * plane + row) : zero4;
+        cur[s] = ldg4(in_[s] + E.z0 * plane + row);
+    }
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    float rsum = 0.f;
+    int nacc = 0;
+    for (int k = E.z0; k < E.z1; ++k) {
+        const int pk = k * plane;
+        float4 nxt[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) nxt[s] = k + 1 < nz ? ldg4(in_[s] + pk + plane + row) : zero4;
+        const float4 P = cur[0], M = cur[1];
+        const float4 rr = make_float4(P.x * M.x, P.y * M.y, P.z * M.z, P.w * M.w);
+        float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float4 n = cur[s];
+            const float4 u = zero_u ? zero4 : ldg4(in_[s] + pk + row_u);
+            const float4 d = zero_d ? zero4 : ldg4(in_[s] + pk + row_d);
+            float l = __shfl_up_sync(0xffffffffu, n.w, 1);
+            float r = __shfl_down_sync(0xffffffffu, n.x, 1);
+            if (need_l) l = zero_l ? 0.f : __ldg(in_[s] + pk + row_l);
+            if (need_r) r = zero_r ? 0.f : __ldg(in_[s] + pk + row_r);
+            const float4 zm = prev[s], zp = nxt[s];
+            const float w0 = c.w0[s], wx = c.wx[s], wy = c.wy[s], wzm = c.wzm[s], wzp = c.wzp[s], adt = c.adt;
+            float4 v;
+            v.x = upd7(n.x, l, n.y, u.x, d.x, zm.x, zp.x, rr.x, w0, wx, wy, wzm, wzp, adt);
+            v.y = upd7(n.y, n.x, n.z, u.y, d.y, zm.y, zp.y, rr.y, w0, wx, wy, wzm, wzp, adt);
+            v.z = upd7(n.z, n.y, n.w, u.z, d.z, zm.z, zp.z, rr.z, w0, wx, wy, wzm, wzp, adt);
+            v.w = upd7(n.w, n.z, r, u.w, d.w, zm.w, zp.w, rr.w, w0, wx, wy, wzm, wzp, adt);
+            if (valid) {
+                *reinterpret_cast<float4 *>(out_[s] + pk + row) = v;
+                if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
+                if (!PERIODIC) {
+                    if (c4 == 0) lat[s] += n.x;
+                    if (c4 == ncol4 - 1) lat[s] += n.w;
+                    if (edge_u) lat[s] += (n.x + n.y) + (n.z + n.w);
+                    if (edge_d) lat[s] += (n.x + n.y) + (n.z + n.w);
+                }
+            }
+            prev[s] = n;
+            cur[s] = nxt[s];
+        }
+        if (valid) rsum += (rr.x + rr.y) + (rr.z + rr.w);
+        if (++nacc == 32) { acc[0] += (double)rsum; rsum = 0.f; nacc = 0; }
+        if (k == 0) { acc[1] += (double)an[0]; acc[2] += (double)an[1]; }
+        if (k == nz - 1) { acc[3] += (double)an[0]; acc[4] += (double)an[1]; }
+        if (!PERIODIC) {
+            acc[5] += (double)lat[0] * c.latx_f[0];
+            acc[6] += (double)lat[1] * c.latx_f[1];
+        }
+    }
+    acc[0] += (double)rsum;
+    block_sum<7>(acc, red);
+    if (threadIdx.x == 0) {
+        double *sl = slots + (size_t)blockIdx.x * NT;
+        sl[0] += acc[0] * c.rec_f;
+        sl[1] += acc[1] * c.anode_f[0];
+        sl[2] += acc[2] * c.anode_f[1];
+        sl[3] += acc[3] * c.cathode_f[0];
+        sl[4] += acc[4] * c.cathode_f[1];
+        sl[5] += acc[5];
+        sl[6] += acc[6];
+    }
+}
+
+// Fold the slots of each active simulation's entries (contiguous in the
+// table, in order) into its FP64 accumulators and clear them.  One block
+// per active simulation, one thread per tally.
+__global__ void batch_fold_kernel(const int *__restrict__ first, const int *__restrict__ count,
+                                  const int *__restrict__ sim_of, double *__restrict__ slots,
+                                  double *__restrict__ acc) {
+    const int a = blockIdx.x, q = threadIdx.x;
+    if (q >= NT) return;
+    double s = 0.0;
+    for (int e = first[a]; e < first[a] + count[a]; ++e) {
+        s += slots[(size_t)e * NT + q];
+        slots[(size_t)e * NT + q] = 0.0;
+    }
+    acc[(size_t)sim_of[a] * NT + q] += s;
+}
+
+// Per-entry sums of n+ and n- (FP64), for the in-domain charge.
+__global__ void __launch_bounds__(256)
+batch_monitor_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restrict__ tab,
+                     const float *__restrict__ ip_all, const float *__restrict__ im_all, double *__restrict__ mon) {
+    __shared__ double red[32 * 2];
+    const BatchEntry E = tab[blockIdx.x];
+    const long long off = sims[E.sim].off;
+    const long long nxs = sims[E.sim].nx;
+    double v[2] = {0.0, 0.0};
+    for (size_t idx = (size_t)(E.begin * nxs) + threadIdx.x; idx < (size_t)(E.end * nxs); idx += blockDim.x) {
+        v[0] += (double)ip_all[off + idx];
+        v[1] += (double)im_all[off + idx];
+    }
+    block_sum<2>(v, red);
+    if (threadIdx.x == 0) {
+        mon[2 * blockIdx.x] = v[0];
+        mon[2 * blockIdx.x + 1] = v[1];
+    }
+}
+
+// Per-entry maximum of n+ and n-.
+__global__ void __launch_bounds__(256)
+batch_max_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restrict__ tab,
+                 const float *__restrict__ ip_all, const float *__restrict__ im_all, float *__restrict__ mx) {
+    __shared__ float red[32];
+    const BatchEntry E = tab[blockIdx.x];
+    const long long off = sims[E.sim].off;
+    const long long nxs = sims[E.sim].nx;
+    float v = -INFINITY;
+    for (size_t idx = (size_t)(E.begin * nxs) + threadIdx.x; idx < (size_t)(E.end * nxs); idx += blockDim.x)
+        v = fmaxf(v, fmaxf(ip_all[off + idx], im_all[off + idx]));
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, red[w]);
+        mx[blockIdx.x] = v;
+    }
+}
+
+}  // namespace itk
+
+using namespace itk;
+
+struct it_batch {
+    int nsim;
+    it_params p;
+    std::vector<it_sim_desc> desc;
+    std::vector<BatchSim> hs;         // host copy of the descriptors
+    std::vector<double> dx;
+    std::vector<double> dt;
+    size_t total;                     // elements per state array
+    float *state[2][2];               // [set][species]
+    void *state_base;
+    BatchSim *d_sims;
+    double *d_acc;                    // [nsim][NT] folded tallies
+    double *d_rel;                    // [nsim][8] released (DevAcc layout)
+    // work tables of the current segment
+    std::vector<BatchEntry> tab;      // row ranges of every active simulation (monitors)
+    std::vector<int> mfirst, mcount;  // per active simulation, into tab
+    std::vector<VecEntry> vtab;       // step entries of the float4 kernel
+    std::vector<BatchEntry> stab;     // step entries of the scalar kernel
+    std::vector<int> first, count, sim_of;   // per active simulation, into the step slots
+    BatchEntry *d_tab, *d_stab;
+    VecEntry *d_vtab;
+    int *d_first, *d_count, *d_simof;
+    double *d_slots, *d_mon;
+    size_t tab_cap, stab_cap, vtab_cap, slot_cap, act_cap;
+    long long chunk;                  // cells per entry
+    // per simulation
+    std::vector<int64_t> steps;
+    std::vector<char> active;
+    int64_t bstep;                    // steps taken by every active simulation
+    cudaStream_t stream;
+    cudaGraphExec_t graph;
+    int graph_len, graph_parity;
+    bool tab_dirty;
+    // deposition scratch (sized for the largest simulation)
+    double *d_plane, *d_tracks, *d_wx, *d_wy;
+    int64_t track_cap;
+    int max_nx, max_ny;
+};
+
+namespace {
+
+int bfail(int code, const std::string &m) {
+    set_error(m);
+    return code;
+}
+
+// Rebuild the work tables for the active simulations.  Step entries: the
+// float4 kernel takes simulations with nx % 4 == 0 (tiles of 256/(nx/4)
+// rows, split in z when few cells are active), the scalar kernel the rest.
+// All entries of one simulation are contiguous, so the fold is in order.
+int build_table(it_batch *b) {
+    b->tab.clear(); b->mfirst.clear(); b->mcount.clear();
+    b->vtab.clear(); b->stab.clear();
+    b->first.clear(); b->count.clear(); b->sim_of.clear();
+    long long active_cells = 0, vec_tiles = 0;
+    for (int s = 0; s < b->nsim; ++s) {
+        if (!b->active[s]) continue;
+        const BatchSim &h = b->hs[s];
+        active_cells += (long long)h.nx * h.ny * h.nz;
+        if (h.nx % 4 == 0 && h.nx <= 1024) {
+            const int rows = std::max(1, 256 / (h.nx / 4));
+            vec_tiles += (h.ny + rows - 1) / rows;
+        }
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long chunk = std::max(1024LL, std::min(b->chunk, active_cells / (4LL * sms)));
+    // z splits so that the float4 launch keeps about 4 CTAs per SM busy
+    const long long zsplit = vec_tiles > 0 ? std::max(1LL, (4LL * sms + vec_tiles - 1) / vec_tiles) : 1;
+    std::vector<int> vfirst, vcount, sfirst, scount, vsim, ssim;
+    for (int s = 0; s < b->nsim; ++s) {
+        if (!b->active[s]) continue;
+        const BatchSim &h = b->hs[s];
+        const long long rows = (long long)h.ny * h.nz;
+        const long long rpe = std::max(1LL, chunk / h.nx);
+        b->mfirst.push_back((int)b->tab.size());
+        int n = 0;
+        for (long long r0 = 0; r0 < rows; r0 += rpe, ++n) b->tab.push_back(BatchEntry{s, 0, r0, std::min(rows, r0 + rpe)});
+        b->mcount.push_back(n);
+        if (h.nx % 4 == 0 && h.nx <= 1024) {
+            const int rpt = std::max(1, 256 / (h.nx / 4));
+            const int zc = (int)std::min<long long>(zsplit, std::max(1, h.nz / 8));
+            vsim.push_back(s);
+            vfirst.push_back((int)b->vtab.size());
+            int m = 0;
+            for (int y0 = 0; y0 < h.ny; y0 += rpt)
+                for (int q = 0; q < zc; ++q, ++m)
+                    b->vtab.push_back(VecEntry{s, y0, std::min(rpt, h.ny - y0), (int)((long long)h.nz * q / zc),
+                                               (int)((long long)h.nz * (q + 1) / zc), 0});
+            vcount.push_back(m);
+        } else {
+            ssim.push_back(s);
+            sfirst.push_back((int)b->stab.size());
+            int m = 0;
+            for (long long r0 = 0; r0 < rows; r0 += rpe, ++m) b->stab.push_back(BatchEntry{s, 0, r0, std::min(rows, r0 + rpe)});
+            scount.push_back(m);
+        }
+    }
+    // step slots: [float4 entries][scalar entries]
+    const int nv = (int)b->vtab.size();
+    for (size_t q = 0; q < vsim.size(); ++q) { b->sim_of.push_back(vsim[q]); b->first.push_back(vfirst[q]); b->count.push_back(vcount[q]); }
+    for (size_t q = 0; q < ssim.size(); ++q) { b->sim_of.push_back(ssim[q]); b->first.push_back(nv + sfirst[q]); b->count.push_back(scount[q]); }
+    const size_t ne = b->tab.size(), nvs = b->vtab.size(), nss = b->stab.size(), na = b->sim_of.size();
+    const size_t nslot = nvs + nss;
+    auto grow = [&](void **p, size_t &cap, size_t need, size_t esz) -> cudaError_t {
+        if (need <= cap) return cudaSuccess;
+        cudaFree(*p);
+        *p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(p, esz * need);
+        if (e == cudaSuccess) cap = need;
+        return e;
+    };
+    size_t mon_cap = b->tab_cap;
+    IT_CK(grow((void **)&b->d_tab, b->tab_cap, ne, sizeof(BatchEntry)));
+    if (b->tab_cap != mon_cap || !b->d_mon) {
+        cudaFree(b->d_mon);
+        b->d_mon = nullptr;
+        IT_CK(cudaMalloc(&b->d_mon, sizeof(double) * 2 * std::max<size_t>(b->tab_cap, 1)));
+    }
+    IT_CK(grow((void **)&b->d_vtab, b->vtab_cap, nvs, sizeof(VecEntry)));
+    IT_CK(grow((void **)&b->d_stab, b->stab_cap, nss, sizeof(BatchEntry)));
+    IT_CK(grow((void **)&b->d_slots, b->slot_cap, nslot, sizeof(double) * NT));
+    if (na > b->act_cap) {
+        cudaFree(b->d_first); cudaFree(b->d_count); cudaFree(b->d_simof);
+        IT_CK(cudaMalloc(&b->d_first, sizeof(int) * na));
+        IT_CK(cudaMalloc(&b->d_count, sizeof(int) * na));
+        IT_CK(cudaMalloc(&b->d_simof, sizeof(int) * na));
+        b->act_cap = na;
+    }
+    if (ne) IT_CK(cudaMemcpyAsync(b->d_tab, b->tab.data(), sizeof(BatchEntry) * ne, cudaMemcpyHostToDevice, b->stream));
+    if (nvs) IT_CK(cudaMemcpyAsync(b->d_vtab, b->vtab.data(), sizeof(VecEntry) * nvs, cudaMemcpyHostToDevice, b->stream));
+    if (nss) IT_CK(cudaMemcpyAsync(b->d_stab, b->stab.data(), sizeof(BatchEntry) * nss, cudaMemcpyHostToDevice, b->stream));
+    if (nslot) IT_CK(cudaMemsetAsync(b->d_slots, 0, sizeof(double) * NT * nslot, b->stream));
+    if (na) {
+        IT_CK(cudaMemcpyAsync(b->d_first, b->first.data(), sizeof(int) * na, cudaMemcpyHostToDevice, b->stream));
+        IT_CK(cudaMemcpyAsync(b->d_count, b->count.data(), sizeof(int) * na, cudaMemcpyHostToDevice, b->stream));
+        IT_CK(cudaMemcpyAsync(b->d_simof, b->sim_of.data(), sizeof(int) * na, cudaMemcpyHostToDevice, b->stream));
+    }
+    IT_CK(cudaStreamSynchronize(b->stream));   // host vectors may change at the next rebuild
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    b->tab_dirty = false;
+    return IT_OK;
+}
+
+int launch_batched_step(it_batch *b, int parity) {
+    const int nv = (int)b->vtab.size(), ns = (int)b->stab.size();
+    const float *ip = b->state[parity][0], *im = b->state[parity][1];
+    float *op = b->state[parity ^ 1][0], *om = b->state[parity ^ 1][1];
+    const bool per = b->p.lateral_bc == IT_PERIODIC;
+    if (nv) {
+        if (per) step_batched_vec_kernel<true><<<nv, 256, 0, b->stream>>>(b->d_sims, b->d_vtab, ip, im, op, om, b->d_slots);
+        else step_batched_vec_kernel<false><<<nv, 256, 0, b->stream>>>(b->d_sims, b->d_vtab, ip, im, op, om, b->d_slots);
+        IT_CK(cudaGetLastError());
+    }
+    if (ns) {
+        double *sl = b->d_slots + (size_t)NT * nv;
+        if (per) step_batched_kernel<true><<<ns, 256, 0, b->stream>>>(b->d_sims, b->d_stab, ip, im, op, om, sl);
+        else step_batched_kernel<false><<<ns, 256, 0, b->stream>>>(b->d_sims, b->d_stab, ip, im, op, om, sl);
+        IT_CK(cudaGetLastError());
+    }
+    return IT_OK;
+}
+
+// K steps of every active simulation (K even: the graph returns to the same set)
+int run_segment(it_batch *b, int K) {
+    const int parity = (int)(b->bstep & 1);
+    if (!b->graph || b->graph_len != K || b->graph_parity != parity) {
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        IT_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = IT_OK;
+        for (int q = 0; q < K && rc == IT_OK; ++q) rc = launch_batched_step(b, parity ^ (q & 1));
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(batch)");
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate(batch)"); }
+        b->graph_len = K;
+        b->graph_parity = parity;
+    }
+    IT_CK(cudaGraphLaunch(b->graph, b->stream));
+    b->bstep += K;
+    for (int s = 0; s < b->nsim; ++s)
+        if (b->active[s]) b->steps[s] += K;
+    return IT_OK;
+}
+
+int fold(it_batch *b) {
+    const int na = (int)b->sim_of.size();
+    if (!na) return IT_OK;
+    batch_fold_kernel<<<na, 32, 0, b->stream>>>(b->d_first, b->d_count, b->d_simof, b->d_slots, b->d_acc);
+    IT_CK(cudaGetLastError());
+    return IT_OK;
+}
+
+// in-domain ions of every simulation in the current table
+int in_domain(it_batch *b, std::vector<double> &ind2) {
+    ind2.assign(2 * (size_t)b->nsim, 0.0);
+    const int ne = (int)b->tab.size();
+    if (!ne) return IT_OK;
+    const int parity = (int)(b->bstep & 1);
+    batch_monitor_kernel<<<ne, 256, 0, b->stream>>>(b->d_sims, b->d_tab, b->state[parity][0], b->state[parity][1],
+                                                    b->d_mon);
+    IT_CK(cudaGetLastError());
+    std::vector<double> mon(2 * (size_t)ne);
+    IT_CK(cudaMemcpyAsync(mon.data(), b->d_mon, sizeof(double) * 2 * ne, cudaMemcpyDeviceToHost, b->stream));
+    IT_CK(cudaStreamSynchronize(b->stream));
+    int a = 0;
+    for (int s = 0; s < b->nsim; ++s) {
+        if (!b->active[s]) continue;
+        const double vol = b->dx[s] * b->dx[s] * b->dx[s];
+        double p = 0, m = 0;
+        for (int e = b->mfirst[a]; e < b->mfirst[a] + b->mcount[a]; ++e) { p += mon[2 * e]; m += mon[2 * e + 1]; }
+        ++a;
+        ind2[2 * s] = p * vol;
+        ind2[2 * s + 1] = m * vol;
+    }
+    return IT_OK;
+}
+
+void batch_free(it_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->state_base);
+    cudaFree(b->d_sims); cudaFree(b->d_acc); cudaFree(b->d_rel);
+    cudaFree(b->d_tab); cudaFree(b->d_slots); cudaFree(b->d_mon);
+    cudaFree(b->d_vtab); cudaFree(b->d_stab);
+    cudaFree(b->d_first); cudaFree(b->d_count); cudaFree(b->d_simof);
+    cudaFree(b->d_plane); cudaFree(b->d_tracks); cudaFree(b->d_wx); cudaFree(b->d_wy);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *common, it_batch **out) {
+    if (!out) return bfail(IT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nsim < 1 || !descs || !common) return bfail(IT_EINVAL, "need at least one simulation descriptor");
+    if (common->precision != IT_FP32) return bfail(IT_EINVAL, "batched simulations use FP32 densities");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bfail(IT_ECUDA, "no CUDA device available");
+    it_batch *b = new (std::nothrow) it_batch();
+    if (!b) return bfail(IT_ENOMEM, "host allocation failed");
+    b->nsim = nsim;
+    b->p = *common;
+    b->desc.assign(descs, descs + nsim);
+    b->hs.resize(nsim);
+    b->dx.resize(nsim);
+    b->dt.resize(nsim);
+    b->steps.assign(nsim, 0);
+    b->active.assign(nsim, 1);
+    b->chunk = 16384;
+    b->graph_parity = -1;
+    size_t off = 0;
+    for (int s = 0; s < nsim; ++s) {
+        const it_sim_desc &d = descs[s];
+        it_params p = *common;
+        p.gap_cm = d.nz * d.dx_cm;
+        p.voltage_V = d.voltage_V;
+        p.n_peak_cm3 = d.n_peak_cm3;
+        it_grid g{d.nx, d.ny, d.nz};
+        double dt = d.dt_s;
+        if (!(dt > 0)) {
+            int rc = it_auto_dt(&p, d.dx_cm, &dt);
+            if (rc) { batch_free(b); return rc; }
+        }
+        int rc = validate_step_args(&p, g, d.dx_cm, dt);
+        if (rc) {
+            std::string m = it_last_error();
+            batch_free(b);
+            return bfail(rc, "simulation " + std::to_string(s) + ": " + m);
+        }
+        if ((long long)d.nx * d.ny * d.nz > 0x7fffffffLL) {
+            batch_free(b);
+            return bfail(IT_EINVAL, "simulation " + std::to_string(s) + ": more than 2^31 - 1 cells");
+        }
+        BatchSim &h = b->hs[s];
+        h.nx = d.nx; h.ny = d.ny; h.nz = d.nz; h.pad = 0;
+        h.off = (long long)off;
+        coef_f32(&p, d.dx_cm, dt, &h.cf);
+        b->dx[s] = d.dx_cm;
+        b->dt[s] = dt;
+        const size_t cells = (size_t)d.nx * d.ny * d.nz;
+        off += (cells + 63) / 64 * 64;   // 256-byte aligned per simulation
+        b->max_nx = std::max(b->max_nx, d.nx);
+        b->max_ny = std::max(b->max_ny, d.ny);
+    }
+    b->total = off;
+    auto bail = [&](cudaError_t e, const char *what) {
+        int rc = e == cudaErrorMemoryAllocation ? bfail(IT_ENOMEM, what) : cuda_fail(e, what);
+        batch_free(b);
+        return rc;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
+    if ((e = cudaMalloc(&b->state_base, sizeof(float) * 4 * off)) != cudaSuccess) return bail(e, "batch state");
+    float *base = (float *)b->state_base;
+    b->state[0][0] = base; b->state[0][1] = base + off; b->state[1][0] = base + 2 * off; b->state[1][1] = base + 3 * off;
+    if ((e = cudaMemsetAsync(b->state_base, 0, sizeof(float) * 4 * off, b->stream)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMalloc(&b->d_sims, sizeof(BatchSim) * nsim)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_acc, sizeof(double) * NT * nsim)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_rel, sizeof(double) * 8 * nsim)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_plane, sizeof(double) * b->max_nx * b->max_ny)) != cudaSuccess)
+        return bail(e, "batch scratch");
+    if ((e = cudaMemcpyAsync(b->d_sims, b->hs.data(), sizeof(BatchSim) * nsim, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_acc, 0, sizeof(double) * NT * nsim, b->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_rel, 0, sizeof(double) * 8 * nsim, b->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+        return bail(e, "batch setup");
+    b->tab_dirty = true;
+    *out = b;
+    return IT_OK;
+}
+
+int it_batch_deposit_tracks(it_batch *b, int32_t sim, int64_t n, const double *xy, const double *let,
+                            const double *bb) {
+    if (!b || sim < 0 || sim >= b->nsim) return bfail(IT_EINVAL, "bad batch or simulation index");
+    if (b->bstep != 0) return bfail(IT_ESTATE, "tracks are deposited before the first step");
+    if (n < 0 || (n > 0 && (!xy || !let || !bb))) return bfail(IT_EINVAL, "bad track arrays");
+    if (n == 0) return IT_OK;
+    for (int64_t t = 0; t < n; ++t)
+        if (!std::isfinite(xy[2 * t]) || !std::isfinite(xy[2 * t + 1]) || !(let[t] >= 0) || !std::isfinite(let[t]) ||
+            !(bb[t] > 0) || !std::isfinite(bb[t]))
+            return bfail(IT_EINVAL, "track values must be finite with LET >= 0 and b > 0");
+    const it_sim_desc &d = b->desc[sim];
+    // a context view of this simulation for the shared deposition kernels
+    it_ctx *v = new (std::nothrow) it_ctx();
+    if (!v) return bfail(IT_ENOMEM, "host allocation failed");
+    v->g = Grid{d.nx, d.ny, d.nz};
+    v->dx = d.dx_cm;
+    v->p = b->p;
+    v->prec = IT_FP32;
+    v->esize = 4;
+    v->cur = 0;
+    v->n[0][0] = b->state[0][0] + b->hs[sim].off;
+    v->n[0][1] = b->state[0][1] + b->hs[sim].off;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    v->nmon = 2 * sms;
+    v->d_plane = b->d_plane;
+    v->d_acc = b->d_rel + (size_t)8 * sim;
+    int rc = IT_OK;
+    if (n > b->track_cap) {
+        cudaFree(b->d_tracks); cudaFree(b->d_wx); cudaFree(b->d_wy);
+        b->d_tracks = b->d_wx = b->d_wy = nullptr;
+        b->track_cap = 0;
+        cudaError_t e;
+        if ((e = cudaMalloc(&b->d_tracks, sizeof(double) * 4 * n)) != cudaSuccess ||
+            (e = cudaMalloc(&b->d_wx, sizeof(double) * b->max_nx * n)) != cudaSuccess ||
+            (e = cudaMalloc(&b->d_wy, sizeof(double) * b->max_ny * n)) != cudaSuccess) {
+            delete v;
+            return cuda_fail(e, "batch track scratch");
+        }
+        b->track_cap = n;
+    }
+    std::vector<double> packed((size_t)n * 4);
+    for (int64_t t = 0; t < n; ++t) {
+        packed[4 * t] = xy[2 * t]; packed[4 * t + 1] = xy[2 * t + 1];
+        packed[4 * t + 2] = let[t]; packed[4 * t + 3] = bb[t];
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_tracks, packed.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "track upload");
+    v->d_tracks = b->d_tracks; v->d_wx = b->d_wx; v->d_wy = b->d_wy;
+    if (rc == IT_OK) rc = launch_deposit(v, n, b->stream);
+    if (rc == IT_OK) {
+        e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "deposit");
+    }
+    delete v;
+    return rc;
+}
+
+int it_batch_retime(it_batch *b) {
+    if (!b) return bfail(IT_EINVAL, "batch is NULL");
+    if (b->bstep != 0) return bfail(IT_ESTATE, "the time steps can only change before the first step");
+    for (int s = 0; s < b->nsim; ++s) b->active[s] = 1;
+    int rc = build_table(b);
+    if (rc) return rc;
+    const int ne = (int)b->tab.size();
+    float *d_mx = nullptr;
+    IT_CK(cudaMalloc(&d_mx, sizeof(float) * ne));
+    batch_max_kernel<<<ne, 256, 0, b->stream>>>(b->d_sims, b->d_tab, b->state[0][0], b->state[0][1], d_mx);
+    cudaError_t e = cudaGetLastError();
+    std::vector<float> mx(ne);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mx.data(), d_mx, sizeof(float) * ne, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(d_mx);
+    if (e != cudaSuccess) return cuda_fail(e, "batch peak density");
+    int a = -1;
+    for (int s = 0; s < b->nsim; ++s) {
+        ++a;   // every simulation is active here: a indexes mfirst/mcount
+        if (b->desc[s].dt_s > 0) continue;
+        double npk = 0.0;
+        for (int q = b->mfirst[a]; q < b->mfirst[a] + b->mcount[a]; ++q) npk = std::max(npk, (double)mx[q]);
+        if (!std::isfinite(npk)) return bfail(IT_EUNSTABLE, "simulation " + std::to_string(s) + " is not finite");
+        const it_sim_desc &d = b->desc[s];
+        it_params p = b->p;
+        p.gap_cm = d.nz * d.dx_cm;
+        p.voltage_V = d.voltage_V;
+        p.n_peak_cm3 = npk;
+        double dt = 0.0;
+        rc = it_auto_dt(&p, d.dx_cm, &dt);
+        if (rc) return rc;
+        b->dt[s] = dt;
+        coef_f32(&p, d.dx_cm, dt, &b->hs[s].cf);
+    }
+    IT_CK(cudaMemcpyAsync(b->d_sims, b->hs.data(), sizeof(BatchSim) * b->nsim, cudaMemcpyHostToDevice, b->stream));
+    IT_CK(cudaStreamSynchronize(b->stream));
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    return IT_OK;
+}
+
+int it_batch_set_chunk(it_batch *b, int64_t cells_per_block) {
+    if (!b || cells_per_block < 256) return bfail(IT_EINVAL, "chunk must be at least 256 cells");
+    b->chunk = cells_per_block;
+    b->tab_dirty = true;
+    return IT_OK;
+}
+
+int it_batch_run(it_batch *b, double tol, int64_t max_steps, int64_t check_every, int64_t *launches) {
+    if (!b) return bfail(IT_EINVAL, "batch is NULL");
+    if (!(tol >= 0) || max_steps < 0 || check_every < 2) return bfail(IT_EINVAL, "bad argument");
+    const int K = (int)(check_every + (check_every & 1));
+    std::vector<double> rel(8 * (size_t)b->nsim);
+    IT_CK(cudaMemcpyAsync(rel.data(), b->d_rel, sizeof(double) * 8 * b->nsim, cudaMemcpyDeviceToHost, b->stream));
+    IT_CK(cudaStreamSynchronize(b->stream));
+    int64_t nl = 0;
+    std::vector<double> ind;
+    for (;;) {
+        if (b->tab_dirty) {
+            int rc = build_table(b);
+            if (rc) return rc;
+        }
+        // completion of every active simulation
+        int rc = in_domain(b, ind);
+        if (rc) return rc;
+        bool changed = false;
+        for (size_t a = 0; a < b->sim_of.size(); ++a) {
+            const int s = b->sim_of[a];
+            const double r = rel[8 * s] + rel[8 * s + 1];
+            const double in = ind[2 * s] + ind[2 * s + 1];
+            if (!std::isfinite(in)) return bfail(IT_EUNSTABLE, "simulation " + std::to_string(s) + " is not finite");
+            if (r <= 0 || in / r < tol || b->steps[s] >= max_steps) {
+                b->active[s] = 0;
+                changed = true;
+            }
+        }
+        if (changed) {
+            rc = build_table(b);
+            if (rc) return rc;
+        }
+        if (b->tab.empty()) break;
+        rc = run_segment(b, K);
+        if (rc) return rc;
+        nl += K;
+        rc = fold(b);
+        if (rc) return rc;
+    }
+    if (launches) *launches = nl;
+    IT_CK(cudaStreamSynchronize(b->stream));
+    return IT_OK;
+}
+
+int it_batch_tallies(it_batch *b, int32_t sim, it_tallies_t *t) {
+    if (!b || !t || sim < 0 || sim >= b->nsim) return bfail(IT_EINVAL, "bad argument");
+    double acc[NT], rel[8];
+    IT_CK(cudaMemcpyAsync(acc, b->d_acc + (size_t)NT * sim, sizeof(acc), cudaMemcpyDeviceToHost, b->stream));
+    IT_CK(cudaMemcpyAsync(rel, b->d_rel + (size_t)8 * sim, sizeof(rel), cudaMemcpyDeviceToHost, b->stream));
+    // in-domain charge of this simulation's current set
+    const size_t cells = (size_t)b->hs[sim].nx * b->hs[sim].ny * b->hs[sim].nz;
+    std::vector<float> h(2 * cells);
+    const int parity = (int)(b->steps[sim] & 1);
+    IT_CK(cudaMemcpyAsync(h.data(), b->state[parity][0] + b->hs[sim].off, sizeof(float) * cells,
+                          cudaMemcpyDeviceToHost, b->stream));
+    IT_CK(cudaMemcpyAsync(h.data() + cells, b->state[parity][1] + b->hs[sim].off, sizeof(float) * cells,
+                          cudaMemcpyDeviceToHost, b->stream));
+    IT_CK(cudaStreamSynchronize(b->stream));
+    std::memset(t, 0, sizeof(*t));
+    const double vol = b->dx[sim] * b->dx[sim] * b->dx[sim];
+    for (int s = 0; s < 2; ++s) {
+        double sum = 0, mn = INFINITY, mx = -INFINITY;
+        for (size_t q = 0; q < cells; ++q) {
+            const double v = h[s * cells + q];
+            sum += v; mn = std::min(mn, v); mx = std::max(mx, v);
+        }
+        t->in_domain[s] = sum * vol;
+        t->n_min[s] = mn;
+        t->n_max[s] = mx;
+    }
+    t->recombined = acc[0];
+    t->collected_anode[0] = acc[1]; t->collected_anode[1] = acc[2];
+    t->collected_cathode[0] = acc[3]; t->collected_cathode[1] = acc[4];
+    t->lost_lateral[0] = acc[5]; t->lost_lateral[1] = acc[6];
+    t->released[0] = rel[0]; t->released[1] = rel[1];
+    const double r = rel[0] + rel[1];
+    t->f = r > 0 ? (acc[1] + acc[2] + acc[3] + acc[4]) / r : NAN;
+    t->steps = b->steps[sim];
+    t->dt_s = b->dt[sim];
+    t->t_s = b->dt[sim] * (double)b->steps[sim];
+    return IT_OK;
+}
+
+int it_batch_get_density(it_batch *b, int32_t sim, int species, void *dst, size_t bytes) {
+    if (!b || !dst || sim < 0 || sim >= b->nsim || (species != 0 && species != 1)) return bfail(IT_EINVAL, "bad argument");
+    const size_t cells = (size_t)b->hs[sim].nx * b->hs[sim].ny * b->hs[sim].nz;
+    if (bytes != cells * sizeof(float)) return bfail(IT_EINVAL, "bytes must equal cells * 4");
+    const int parity = (int)(b->steps[sim] & 1);
+    IT_CK(cudaMemcpyAsync(dst, b->state[parity][species] + b->hs[sim].off, bytes, cudaMemcpyDeviceToHost, b->stream));
+    IT_CK(cudaStreamSynchronize(b->stream));
+    return IT_OK;
+}
+
+int it_batch_destroy(it_batch *b) {
+    batch_free(b);
+    return IT_OK;
+}
+
+}  // extern "C"

@@ -462,9 +462,22 @@ static int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx
 
 static int align32f(int floats) { return (floats + 31) / 32 * 32; }   // 128-byte multiple of floats
 
+// The dynamic shared-memory limit is a property of the kernel function,
+// shared by every context: raise it to the device's opt-in maximum (never
+// lower it to one context's need), so launches of other contexts with
+// larger tiles stay valid.
 template <bool P, int I, int W>
 static cudaError_t zm_set_attr(size_t smem) {
-    return cudaFuncSetAttribute(step_zmarch_kernel<P, I, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, step_zmarch_kernel<P, I, W>);
+    if (e != cudaSuccess) return e;
+    const int max_dyn = optin - (int)fa.sharedSizeBytes;   // static shared memory counts against the limit
+    if ((int)smem > max_dyn) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(step_zmarch_kernel<P, I, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
 }
 
 template <bool P, int I, int W>

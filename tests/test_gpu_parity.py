@@ -301,3 +301,21 @@ def test_continuous_512x512x256_full_size():
         for s in range(2):
             assert_density_close(g.density(s), O.density(s), 1e-4)
         compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
+
+
+def test_contexts_with_different_tiles_coexist():
+    # the shared-memory limit of a kernel function is global: a second
+    # context with a smaller tile must not break launches of the first
+    big = B.Simulation(256, 64, 16, 5e-4, 200.0)
+    small = B.Simulation(32, 8, 16, 5e-4, 200.0)
+    try:
+        big.set_launch(B.IT_KERNEL_ZMARCH, 16, 1, 6, 0)
+        small.set_launch(B.IT_KERNEL_ZMARCH, 8, 1, 3, 0)
+        big.deposit([0.05], [0.01], [10.0], [1e-3])
+        small.deposit([0.008], [0.002], [10.0], [1e-3])
+        big.step(8)
+        small.step(8)
+        assert np.isfinite(big.tallies().f) and np.isfinite(small.tallies().f)
+    finally:
+        big.close()
+        small.close()

@@ -441,3 +441,28 @@ def test_uniform_slab_follows_boag_two_voltage_method(u):
         if t.in_domain.sum() / t.released.sum() < 1e-9:
             break
     assert t.f == pytest.approx(o.boag_2vm(u), abs=1e-2)
+
+
+def test_upwind_stays_positive_where_lax_wendroff_undershoots():
+    # With the recombination-bound dt the Courant number is small; the
+    # upwind weights are all non-negative (6 s + c <= 1) and the explicit
+    # recombination factor 1 - alpha dt n stays positive (alpha dt n <= 0.5),
+    # so densities stay >= 0.  Lax-Wendroff at the same dt undershoots below
+    # zero next to the sharp tracks (the source of its divergence at high LET).
+    nx, nz, dx, V = 24, 40, 5e-4, 260.0
+    tr = synth.uniform_tracks(99, 40, nx * dx, nx * dx, 1.2e-3, let=740.0)
+    mins = {}
+    for sch in (o.SCHEME_UPWIND, o.SCHEME_LAX_WENDROFF):
+        probe = o.Oracle(nx, nx, nz, dx, 1e-12, voltage_V=V)
+        probe.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        npk = max(probe.density(0).max(), probe.density(1).max())
+        dt = o.dt_rule(dx, V, nz * dx, MU, DD, ALPHA, n_peak=npk, scheme=sch)
+        O = o.Oracle(nx, nx, nz, dx, dt, voltage_V=V, scheme=sch)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        lo = np.inf
+        for _ in range(6):
+            O.step(20)
+            lo = min(lo, O.density(0).min(), O.density(1).min())
+        mins[sch] = lo
+    assert mins[o.SCHEME_UPWIND] >= 0.0
+    assert mins[o.SCHEME_LAX_WENDROFF] < 0.0
