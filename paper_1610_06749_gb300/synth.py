@@ -227,3 +227,73 @@ def batch_tracks(desc) -> TrackList:
     """Tracks of one batched simulation: uniform (x, y), one LET, one b."""
     return uniform_tracks(desc["seed"], desc["n_tracks"], desc["nx"] * desc["dx_cm"],
                           desc["ny"] * desc["dx_cm"], desc["b_cm"], let=desc["let"])
+
+
+# ---------------------------------------------------------------------------
+# surrogate workload: configurations described by six inputs
+# ---------------------------------------------------------------------------
+
+SURROGATE_SECTION_CM = 0.025     # lateral section 0.25 mm x 0.25 mm (the paper's typical section)
+SURROGATE_CHECK = 64             # pulse periods are whole multiples of this many steps
+
+
+def surrogate_configs(seed: int, n: int):
+    """n seeded configurations for the surrogate.
+
+    Inputs (the six the network sees): LET (log-uniform 1-1000 keV/um),
+    voltage (50-400 V), gap (0.1-0.5 mm), b (5-20 um), tracks per pulse
+    (1-500 on the fixed 0.25 mm section) and pulse period (0 = a single
+    pulse with probability 1/2, else log-uniform 1-30 us for a train of 4
+    pulses).  The grid follows from them: dx = clamp(b/2, 4 um, 8 um), the
+    section and the gap in whole cells (nx a multiple of 4).  Draws per
+    configuration: 8 uniforms.
+    """
+    u = uniform01(seed, 8 * n).reshape(n, 8)
+    out = []
+    for k in range(n):
+        let = 10.0 ** (3.0 * u[k, 0])
+        V = 50.0 + 350.0 * u[k, 1]
+        gap = 0.01 + 0.04 * u[k, 2]
+        b = (5.0 + 15.0 * u[k, 3]) * 1e-4
+        ntr = 1 + int(u[k, 4] * 500)
+        period = 0.0 if u[k, 5] < 0.5 else 10.0 ** (-6.0 + 1.5 * u[k, 6])
+        dx = min(max(b / 2.0, 4e-4), 8e-4)
+        nx = max(8, int(round(SURROGATE_SECTION_CM / dx / 4.0)) * 4)
+        nz = max(8, int(round(gap / dx)))
+        out.append(dict(let=let, voltage_V=V, b_cm=b, n_tracks=ntr, period_s=period,
+                        pulses=1 if period == 0.0 else 4, nx=nx, ny=nx, nz=nz, dx_cm=dx,
+                        gap_cm=nz * dx, seed=seed * 100003 + k))
+    return out
+
+
+def surrogate_tracks(cfg) -> TrackList:
+    """Tracks of one pulse of a surrogate configuration (uniform x, y)."""
+    L = cfg["nx"] * cfg["dx_cm"]
+    return uniform_tracks(cfg["seed"], cfg["n_tracks"], L, L, cfg["b_cm"], let=cfg["let"])
+
+
+def surrogate_features(cfg, period_s=None) -> np.ndarray:
+    """The six network inputs: log10 LET, V, gap (cm), b (cm), tracks per
+    pulse, pulse period (s; the period actually simulated when given)."""
+    p = cfg["period_s"] if period_s is None else period_s
+    return np.array([math.log10(cfg["let"]), cfg["voltage_V"], cfg["gap_cm"], cfg["b_cm"],
+                     float(cfg["n_tracks"]), p], dtype=np.float64)
+
+
+def mlp_init(seed: int, members: int = 5) -> np.ndarray:
+    """Initial surrogate weights, [members][n_params] float64: every weight
+    uniform in [-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64, biases 0.
+    Layout per member: W1 [256][6], b1, W2 [256][256], b2, W3, b3, W4, b4,
+    W5 [1][256], b5."""
+    shapes = [(256, 6), (256,), (256, 256), (256,), (256, 256), (256,), (256, 256), (256,), (1, 256), (1,)]
+    n = int(sum(np.prod(s) for s in shapes))
+    out = np.zeros((members, n))
+    for m in range(members):
+        o = 0
+        for q, s in enumerate(shapes):
+            k = int(np.prod(s))
+            if len(s) == 2:
+                u = uniform01(seed * 7 + 1000 * m + q, k)
+                out[m, o:o + k] = (2.0 * u - 1.0) / math.sqrt(s[1])
+            o += k
+    return out
