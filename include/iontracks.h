@@ -272,9 +272,17 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
 int it_batch_deposit_tracks(it_batch *b, int32_t sim, int64_t n, const double *xy_cm,
                             const double *let_keV_um, const double *b_cm);
 
-/* After the deposits and before the first step: every simulation created
- * with dt_s <= 0 gets it_auto_dt with n_peak = the largest density of its
- * deposited state (IT_ESTATE after the first step). */
+/* Make simulation `sim` a train of `count` identical pulses: the tracks
+ * deposited with it_batch_deposit_tracks are deposited again at the start
+ * of steps period_steps, 2 period_steps, ...  (period_steps must be a
+ * multiple of the even check interval of it_batch_run).  Before the first
+ * step only. */
+int it_batch_set_pulses(it_batch *b, int32_t sim, int32_t count, int64_t period_steps);
+
+/* After the deposits (and it_batch_set_pulses) and before the first step:
+ * every simulation created with dt_s <= 0 gets it_auto_dt with n_peak = the
+ * largest density of its deposited state times its pulse count (IT_ESTATE
+ * after the first step). */
 int it_batch_retime(it_batch *b);
 
 /* Cells per work-table entry (one CTA each; default 16384). */
@@ -293,6 +301,54 @@ int it_batch_get_density(it_batch *b, int32_t sim, int species, void *host_dst, 
 
 /* Free a batch; NULL is a no-op. */
 int it_batch_destroy(it_batch *b);
+
+/* ---------------------------------------------------------------------------
+ * Surrogate network for f: an ensemble of perceptrons 6 -> 256 -> 256 ->
+ * 256 -> 256 -> 1 (SiLU hidden layers, sigmoid output) trained by mean
+ * squared error with Adam on solver results.  bfloat16 weights in the
+ * matrix products, FP32 accumulation on the tensor cores, FP32 master
+ * weights; reductions in a fixed order.  Inputs per sample (doubles, row
+ * of 6): log10 LET (keV/um), voltage (V), gap (cm), b (cm), tracks per
+ * pulse, pulse period (s, 0 for a single pulse); they are normalised with
+ * the mean/std given to (or fitted by) the network.  The paper has no
+ * counterpart: the surrogate answers f quickly and hands a configuration
+ * back to the solver when its members disagree.
+ * Parameter layout per member (floats): W1 [256][6], b1 [256], W2
+ * [256][256], b2, W3, b3, W4, b4, W5 [1][256], b5 [1].
+ * ------------------------------------------------------------------------- */
+#define IT_MLP_INPUTS 6
+#define IT_MLP_HIDDEN 256
+#define IT_MLP_PARAMS 199425
+
+typedef struct it_mlp it_mlp;
+
+/* Create an ensemble of `members` networks (weights zero until set) with
+ * work space for batches of up to max_batch samples. */
+int it_mlp_create(int32_t members, int32_t max_batch, it_mlp **out);
+/* Set / read one member's FP32 master parameters (count = IT_MLP_PARAMS);
+ * setting restarts the optimiser state. */
+int it_mlp_set_params(it_mlp *net, int32_t member, const float *params, int64_t count);
+int it_mlp_get_params(it_mlp *net, int32_t member, float *out, int64_t count);
+/* Input normalisation x' = (x - mean) / std (6 values each, std > 0), or
+ * fitted to n samples. */
+int it_mlp_set_normalization(it_mlp *net, const double *mean6, const double *std6);
+int it_mlp_fit_normalization(it_mlp *net, int64_t n, const double *x);
+/* Training set: n samples x (6 doubles), targets y (n doubles). */
+int it_mlp_set_data(it_mlp *net, int64_t n, const double *x, const double *y);
+/* `epochs` passes of Adam (beta 0.9 / 0.999, eps 1e-8, rate lr) over
+ * mini-batches of `batch` samples in a SplitMix64 Fisher-Yates order from
+ * `seed`; every member sees the same batches.  loss_per_epoch (may be NULL)
+ * receives the mean over batches and members of the batch loss. */
+int it_mlp_train(it_mlp *net, int32_t epochs, int32_t batch, double lr, uint64_t seed, double *loss_per_epoch);
+/* Loss and gradient of every member on n <= max_batch samples (no update):
+ * grads: members x IT_MLP_PARAMS floats, loss: members doubles.  The next
+ * it_mlp_adam_step applies this gradient. */
+int it_mlp_loss_grad(it_mlp *net, int64_t n, const double *x, const double *y, float *grads, double *loss);
+int it_mlp_adam_step(it_mlp *net, double lr);
+/* Predictions for n samples: ensemble mean and spread (max - min), and each
+ * member's value (n x members, may be NULL). */
+int it_mlp_predict(it_mlp *net, int64_t n, const double *x, double *mean, double *spread, double *per_member);
+int it_mlp_destroy(it_mlp *net);
 
 /* Capacity (CTAs) of the fixed tally scratch used by it_step_noalloc. */
 #define IT_NOALLOC_MAX_BLOCKS 2048

@@ -104,10 +104,22 @@ def lib():
                                     ctypes.POINTER(P)]),
             "it_batch_deposit_tracks": (I, [P, ctypes.c_int32, I64, DP, DP, DP]),
             "it_batch_set_chunk": (I, [P, I64]),
+            "it_batch_set_pulses": (I, [P, ctypes.c_int32, ctypes.c_int32, I64]),
             "it_batch_run": (I, [P, D, I64, I64, I64P]),
             "it_batch_tallies": (I, [P, ctypes.c_int32, ctypes.POINTER(it_tallies_t)]),
             "it_batch_get_density": (I, [P, ctypes.c_int32, I, P, SZ]),
             "it_batch_destroy": (I, [P]),
+            "it_mlp_create": (I, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(P)]),
+            "it_mlp_set_params": (I, [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), I64]),
+            "it_mlp_get_params": (I, [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), I64]),
+            "it_mlp_set_normalization": (I, [P, DP, DP]),
+            "it_mlp_fit_normalization": (I, [P, I64, DP]),
+            "it_mlp_set_data": (I, [P, I64, DP, DP]),
+            "it_mlp_train": (I, [P, ctypes.c_int32, ctypes.c_int32, D, ctypes.c_uint64, DP]),
+            "it_mlp_loss_grad": (I, [P, I64, DP, DP, ctypes.POINTER(ctypes.c_float), DP]),
+            "it_mlp_adam_step": (I, [P, D]),
+            "it_mlp_predict": (I, [P, I64, DP, DP, DP, DP]),
+            "it_mlp_destroy": (I, [P]),
             "it_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
@@ -295,6 +307,10 @@ def it_batch_deposit_tracks(h, sim, xy_cm, let_keV_um, b_cm):
     _check(lib().it_batch_deposit_tracks(h, int(sim), L.size, _dp(xy), _dp(L), _dp(b)))
 
 
+def it_batch_set_pulses(h, sim, count, period_steps):
+    _check(lib().it_batch_set_pulses(h, int(sim), int(count), int(period_steps)))
+
+
 def it_batch_set_chunk(h, cells_per_block):
     _check(lib().it_batch_set_chunk(h, int(cells_per_block)))
 
@@ -319,6 +335,76 @@ def it_batch_get_density(h, sim, species, out: np.ndarray):
 def it_batch_destroy(h):
     if h:
         _check(lib().it_batch_destroy(h))
+
+
+IT_MLP_INPUTS, IT_MLP_HIDDEN, IT_MLP_PARAMS = 6, 256, 199425
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def it_mlp_create(members=5, max_batch=1024):
+    h = ctypes.c_void_p()
+    _check(lib().it_mlp_create(int(members), int(max_batch), ctypes.byref(h)))
+    return h
+
+
+def it_mlp_set_params(h, member, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().it_mlp_set_params(h, int(member), _fp(a), a.size))
+
+
+def it_mlp_get_params(h, member):
+    out = np.empty(IT_MLP_PARAMS, dtype=np.float32)
+    _check(lib().it_mlp_get_params(h, int(member), _fp(out), out.size))
+    return out
+
+
+def it_mlp_set_normalization(h, mean6, std6):
+    m, s = _f64(mean6), _f64(std6)
+    _check(lib().it_mlp_set_normalization(h, _dp(m), _dp(s)))
+
+
+def it_mlp_fit_normalization(h, x):
+    a = _f64(x).reshape(-1, IT_MLP_INPUTS)
+    _check(lib().it_mlp_fit_normalization(h, a.shape[0], _dp(a)))
+
+
+def it_mlp_set_data(h, x, y):
+    a, b = _f64(x).reshape(-1, IT_MLP_INPUTS), _f64(y)
+    _check(lib().it_mlp_set_data(h, a.shape[0], _dp(a), _dp(b)))
+
+
+def it_mlp_train(h, epochs, batch, lr, seed):
+    loss = np.zeros(max(int(epochs), 1))
+    _check(lib().it_mlp_train(h, int(epochs), int(batch), float(lr), ctypes.c_uint64(seed & (2 ** 64 - 1)), _dp(loss)))
+    return loss[:int(epochs)]
+
+
+def it_mlp_loss_grad(h, members, x, y):
+    a, b = _f64(x).reshape(-1, IT_MLP_INPUTS), _f64(y)
+    g = np.empty((members, IT_MLP_PARAMS), dtype=np.float32)
+    loss = np.empty(members)
+    _check(lib().it_mlp_loss_grad(h, a.shape[0], _dp(a), _dp(b), _fp(g), _dp(loss)))
+    return loss, g
+
+
+def it_mlp_adam_step(h, lr):
+    _check(lib().it_mlp_adam_step(h, float(lr)))
+
+
+def it_mlp_predict(h, members, x):
+    a = _f64(x).reshape(-1, IT_MLP_INPUTS)
+    n = a.shape[0]
+    mean, spread, per = np.empty(n), np.empty(n), np.empty((n, members))
+    _check(lib().it_mlp_predict(h, n, _dp(a), _dp(mean), _dp(spread), _dp(per)))
+    return mean, spread, per
+
+
+def it_mlp_destroy(h):
+    if h:
+        _check(lib().it_mlp_destroy(h))
 
 
 # --------------------------------------------------------------------------
@@ -366,6 +452,9 @@ class Batch:
     def deposit(self, sim, x_cm, y_cm, let_keV_um, b_cm):
         xy = np.stack([np.asarray(x_cm, np.float64), np.asarray(y_cm, np.float64)], axis=1)
         it_batch_deposit_tracks(self.h, sim, xy, let_keV_um, b_cm)
+
+    def set_pulses(self, sim, count, period_steps):
+        it_batch_set_pulses(self.h, sim, count, period_steps)
 
     def retime(self):
         """dt of every automatic-dt simulation from its deposited peak density."""

@@ -318,6 +318,11 @@ struct it_batch {
     cudaGraphExec_t graph;
     int graph_len, graph_parity;
     bool tab_dirty;
+    // pulse trains: each simulation's deposited tracks are re-deposited every
+    // period_steps steps until count pulses have been released
+    std::vector<std::vector<double>> pulse_tracks;   // packed [n][4]
+    std::vector<int32_t> pulse_count, pulse_done;
+    std::vector<int64_t> pulse_period;
     // deposition scratch (sized for the largest simulation)
     double *d_plane, *d_tracks, *d_wx, *d_wy;
     int64_t track_cap;
@@ -543,6 +548,10 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
     b->dt.resize(nsim);
     b->steps.assign(nsim, 0);
     b->active.assign(nsim, 1);
+    b->pulse_tracks.assign(nsim, {});
+    b->pulse_count.assign(nsim, 1);
+    b->pulse_done.assign(nsim, 0);
+    b->pulse_period.assign(nsim, 0);
     b->chunk = 16384;
     b->graph_parity = -1;
     size_t off = 0;
@@ -606,17 +615,15 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
     return IT_OK;
 }
 
-int it_batch_deposit_tracks(it_batch *b, int32_t sim, int64_t n, const double *xy, const double *let,
-                            const double *bb) {
-    if (!b || sim < 0 || sim >= b->nsim) return bfail(IT_EINVAL, "bad batch or simulation index");
-    if (b->bstep != 0) return bfail(IT_ESTATE, "tracks are deposited before the first step");
-    if (n < 0 || (n > 0 && (!xy || !let || !bb))) return bfail(IT_EINVAL, "bad track arrays");
-    if (n == 0) return IT_OK;
-    for (int64_t t = 0; t < n; ++t)
-        if (!std::isfinite(xy[2 * t]) || !std::isfinite(xy[2 * t + 1]) || !(let[t] >= 0) || !std::isfinite(let[t]) ||
-            !(bb[t] > 0) || !std::isfinite(bb[t]))
-            return bfail(IT_EINVAL, "track values must be finite with LET >= 0 and b > 0");
+}  // extern "C"
+
+namespace {
+
+// Deposit packed tracks [n][4] into simulation `sim`'s current set.
+int deposit_sim(it_batch *b, int sim, const double *packed, int64_t n) {
+    if (n <= 0) return IT_OK;
     const it_sim_desc &d = b->desc[sim];
+    const int parity = (int)(b->steps[sim] & 1);
     // a context view of this simulation for the shared deposition kernels
     it_ctx *v = new (std::nothrow) it_ctx();
     if (!v) return bfail(IT_ENOMEM, "host allocation failed");
@@ -626,8 +633,8 @@ int it_batch_deposit_tracks(it_batch *b, int32_t sim, int64_t n, const double *x
     v->prec = IT_FP32;
     v->esize = 4;
     v->cur = 0;
-    v->n[0][0] = b->state[0][0] + b->hs[sim].off;
-    v->n[0][1] = b->state[0][1] + b->hs[sim].off;
+    v->n[0][0] = b->state[parity][0] + b->hs[sim].off;
+    v->n[0][1] = b->state[parity][1] + b->hs[sim].off;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -648,22 +655,52 @@ int it_batch_deposit_tracks(it_batch *b, int32_t sim, int64_t n, const double *x
         }
         b->track_cap = n;
     }
+    cudaError_t e = cudaMemcpyAsync(b->d_tracks, packed, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "track upload");
+    v->d_tracks = b->d_tracks; v->d_wx = b->d_wx; v->d_wy = b->d_wy;
+    if (rc == IT_OK) rc = launch_deposit(v, n, b->stream);
+    if (rc == IT_OK) {
+        e = cudaStreamSynchronize(b->stream);   // packed host memory may be freed after return
+        if (e != cudaSuccess) rc = cuda_fail(e, "deposit");
+    }
+    delete v;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int it_batch_deposit_tracks(it_batch *b, int32_t sim, int64_t n, const double *xy, const double *let,
+                            const double *bb) {
+    if (!b || sim < 0 || sim >= b->nsim) return bfail(IT_EINVAL, "bad batch or simulation index");
+    if (b->bstep != 0) return bfail(IT_ESTATE, "tracks are deposited before the first step");
+    if (n < 0 || (n > 0 && (!xy || !let || !bb))) return bfail(IT_EINVAL, "bad track arrays");
+    if (n == 0) return IT_OK;
+    for (int64_t t = 0; t < n; ++t)
+        if (!std::isfinite(xy[2 * t]) || !std::isfinite(xy[2 * t + 1]) || !(let[t] >= 0) || !std::isfinite(let[t]) ||
+            !(bb[t] > 0) || !std::isfinite(bb[t]))
+            return bfail(IT_EINVAL, "track values must be finite with LET >= 0 and b > 0");
     std::vector<double> packed((size_t)n * 4);
     for (int64_t t = 0; t < n; ++t) {
         packed[4 * t] = xy[2 * t]; packed[4 * t + 1] = xy[2 * t + 1];
         packed[4 * t + 2] = let[t]; packed[4 * t + 3] = bb[t];
     }
-    cudaError_t e = cudaMemcpyAsync(b->d_tracks, packed.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice,
-                                    b->stream);
-    if (e != cudaSuccess) rc = cuda_fail(e, "track upload");
-    v->d_tracks = b->d_tracks; v->d_wx = b->d_wx; v->d_wy = b->d_wy;
-    if (rc == IT_OK) rc = launch_deposit(v, n, b->stream);
-    if (rc == IT_OK) {
-        e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) rc = cuda_fail(e, "deposit");
-    }
-    delete v;
-    return rc;
+    int rc = deposit_sim(b, sim, packed.data(), n);
+    if (rc) return rc;
+    auto &pt = b->pulse_tracks[sim];
+    pt.insert(pt.end(), packed.begin(), packed.end());
+    b->pulse_done[sim] = 1;
+    return IT_OK;
+}
+
+int it_batch_set_pulses(it_batch *b, int32_t sim, int32_t count, int64_t period_steps) {
+    if (!b || sim < 0 || sim >= b->nsim) return bfail(IT_EINVAL, "bad batch or simulation index");
+    if (b->bstep != 0) return bfail(IT_ESTATE, "pulse trains are set before the first step");
+    if (count < 1 || (count > 1 && period_steps < 1)) return bfail(IT_EINVAL, "need count >= 1 and period_steps >= 1");
+    b->pulse_count[sim] = count;
+    b->pulse_period[sim] = period_steps;
+    return IT_OK;
 }
 
 int it_batch_retime(it_batch *b) {
@@ -688,6 +725,7 @@ int it_batch_retime(it_batch *b) {
         if (b->desc[s].dt_s > 0) continue;
         double npk = 0.0;
         for (int q = b->mfirst[a]; q < b->mfirst[a] + b->mcount[a]; ++q) npk = std::max(npk, (double)mx[q]);
+        npk *= std::max(1, b->pulse_count[s]);   // a train can pile its pulses up
         if (!std::isfinite(npk)) return bfail(IT_EUNSTABLE, "simulation " + std::to_string(s) + " is not finite");
         const it_sim_desc &d = b->desc[s];
         it_params p = b->p;
@@ -717,6 +755,9 @@ int it_batch_run(it_batch *b, double tol, int64_t max_steps, int64_t check_every
     if (!b) return bfail(IT_EINVAL, "batch is NULL");
     if (!(tol >= 0) || max_steps < 0 || check_every < 2) return bfail(IT_EINVAL, "bad argument");
     const int K = (int)(check_every + (check_every & 1));
+    for (int s = 0; s < b->nsim; ++s)
+        if (b->pulse_count[s] > 1 && b->pulse_period[s] % K != 0)
+            return bfail(IT_EINVAL, "simulation " + std::to_string(s) + ": pulse period must be a multiple of the even check interval");
     std::vector<double> rel(8 * (size_t)b->nsim);
     IT_CK(cudaMemcpyAsync(rel.data(), b->d_rel, sizeof(double) * 8 * b->nsim, cudaMemcpyDeviceToHost, b->stream));
     IT_CK(cudaStreamSynchronize(b->stream));
@@ -727,6 +768,23 @@ int it_batch_run(it_batch *b, double tol, int64_t max_steps, int64_t check_every
             int rc = build_table(b);
             if (rc) return rc;
         }
+        // next pulse of a train: deposited at the start of its step
+        bool deposited = false;
+        for (size_t a = 0; a < b->sim_of.size(); ++a) {
+            const int s = b->sim_of[a];
+            const int done = b->pulse_done[s];
+            if (done >= 1 && done < b->pulse_count[s] && b->steps[s] == (int64_t)done * b->pulse_period[s]) {
+                const auto &pt = b->pulse_tracks[s];
+                int rc = deposit_sim(b, s, pt.data(), (int64_t)(pt.size() / 4));
+                if (rc) return rc;
+                b->pulse_done[s] = done + 1;
+                deposited = true;
+            }
+        }
+        if (deposited) {
+            IT_CK(cudaMemcpyAsync(rel.data(), b->d_rel, sizeof(double) * 8 * b->nsim, cudaMemcpyDeviceToHost, b->stream));
+            IT_CK(cudaStreamSynchronize(b->stream));
+        }
         // completion of every active simulation
         int rc = in_domain(b, ind);
         if (rc) return rc;
@@ -736,7 +794,8 @@ int it_batch_run(it_batch *b, double tol, int64_t max_steps, int64_t check_every
             const double r = rel[8 * s] + rel[8 * s + 1];
             const double in = ind[2 * s] + ind[2 * s + 1];
             if (!std::isfinite(in)) return bfail(IT_EUNSTABLE, "simulation " + std::to_string(s) + " is not finite");
-            if (r <= 0 || in / r < tol || b->steps[s] >= max_steps) {
+            const bool pending = b->pulse_done[s] >= 1 && b->pulse_done[s] < b->pulse_count[s];
+            if (r <= 0 || (!pending && in / r < tol) || b->steps[s] >= max_steps) {
                 b->active[s] = 0;
                 changed = true;
             }
