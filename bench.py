@@ -214,6 +214,18 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
             "max_abs_df_vs_plain": df, "df_bound": 1e-3, "scheme": "upwind" if scheme == B.IT_UPWIND else "lax-wendroff"}
 
 
+def surrogate_vs_plain(n_train=2000, n_test=200, epochs=800, plain_sample=40):
+    """The surrogate ensemble (trained on batched-solver runs of the
+    surrogate workload) answering held-out configurations, falling back to the
+    plain solver where its members disagree by more than 1e-3, against the
+    plain solver alone.  Reduced sizes; the full 20k/2k run is
+    `python -m paper_1610_06749_gb300.surrogate`."""
+    from paper_1610_06749_gb300 import surrogate as S
+    out = S.main(["--train", str(n_train), "--test", str(n_test), "--epochs", str(epochs),
+                  "--plain-sample", str(plain_sample)], quiet=True)
+    return out
+
+
 def run_reference(args, ws, rank):
     from paper_1610_06749_gb300 import synth
     import oracle.oracle as o
@@ -359,6 +371,9 @@ def run_ours(args, ws, rank, local):
     batched = None
     if not args.no_batched:
         batched = batched_vs_plain(B, synth)
+    sur = None
+    if not args.no_surrogate and rank == 0:
+        sur = surrogate_vs_plain()
 
     line = None
     if rank == 0:
@@ -389,6 +404,7 @@ def run_ours(args, ws, rank, local):
             "clocks": clocks,
             "f_last": t.f,
             "batched": batched,
+            "surrogate": sur,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -409,6 +425,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain solves/s measurement")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-vs-plain solves/s measurement")
     ap.add_argument("--launch", default="", help="fixed z-march shape TY,ctas_per_sm,stages,grid (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -307,10 +307,10 @@ int it_batch_destroy(it_batch *b);
  * 256 -> 256 -> 1 (SiLU hidden layers, sigmoid output) trained by mean
  * squared error with Adam on solver results.  bfloat16 weights in the
  * matrix products, FP32 accumulation on the tensor cores, FP32 master
- * weights; reductions in a fixed order.  Inputs per sample (doubles, row
- * of 6): log10 LET (keV/um), voltage (V), gap (cm), b (cm), tracks per
- * pulse, pulse period (s, 0 for a single pulse); they are normalised with
- * the mean/std given to (or fitted by) the network.  The paper has no
+ * weights; reductions in a fixed order.  Inputs per sample: a row of 6
+ * doubles describing a configuration (the surrogate workload uses log10 of
+ * LET, voltage, gap, b, tracks per pulse and pulse period + 1 us); they are
+ * normalised with the mean/std given to (or fitted by) the network.  The paper has no
  * counterpart: the surrogate answers f quickly and hands a configuration
  * back to the solver when its members disagree.
  * Parameter layout per member (floats): W1 [256][6], b1 [256], W2
@@ -337,7 +337,7 @@ int it_mlp_fit_normalization(it_mlp *net, int64_t n, const double *x);
 int it_mlp_set_data(it_mlp *net, int64_t n, const double *x, const double *y);
 /* `epochs` passes of Adam (beta 0.9 / 0.999, eps 1e-8, rate lr) over
  * mini-batches of `batch` samples in a SplitMix64 Fisher-Yates order from
- * `seed`; every member sees the same batches.  loss_per_epoch (may be NULL)
+ * `seed`, a different order for every member (ensemble diversity).  loss_per_epoch (may be NULL)
  * receives the mean over batches and members of the batch loss. */
 int it_mlp_train(it_mlp *net, int32_t epochs, int32_t batch, double lr, uint64_t seed, double *loss_per_epoch);
 /* Loss and gradient of every member on n <= max_batch samples (no update):

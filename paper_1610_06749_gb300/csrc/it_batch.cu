@@ -821,24 +821,32 @@ int it_batch_tallies(it_batch *b, int32_t sim, it_tallies_t *t) {
     double acc[NT], rel[8];
     IT_CK(cudaMemcpyAsync(acc, b->d_acc + (size_t)NT * sim, sizeof(acc), cudaMemcpyDeviceToHost, b->stream));
     IT_CK(cudaMemcpyAsync(rel, b->d_rel + (size_t)8 * sim, sizeof(rel), cudaMemcpyDeviceToHost, b->stream));
-    // in-domain charge of this simulation's current set
+    // in-domain charge and extreme densities of this simulation's current set
     const size_t cells = (size_t)b->hs[sim].nx * b->hs[sim].ny * b->hs[sim].nz;
-    std::vector<float> h(2 * cells);
     const int parity = (int)(b->steps[sim] & 1);
-    IT_CK(cudaMemcpyAsync(h.data(), b->state[parity][0] + b->hs[sim].off, sizeof(float) * cells,
-                          cudaMemcpyDeviceToHost, b->stream));
-    IT_CK(cudaMemcpyAsync(h.data() + cells, b->state[parity][1] + b->hs[sim].off, sizeof(float) * cells,
-                          cudaMemcpyDeviceToHost, b->stream));
-    IT_CK(cudaStreamSynchronize(b->stream));
-    std::memset(t, 0, sizeof(*t));
+    constexpr int kMonBlocks = 64;
+    double *d_mon = nullptr;
+    IT_CK(cudaMalloc(&d_mon, sizeof(double) * NM * kMonBlocks));
     const double vol = b->dx[sim] * b->dx[sim] * b->dx[sim];
+    int rc = launch_monitor_raw_f32(b->state[parity][0] + b->hs[sim].off, b->state[parity][1] + b->hs[sim].off,
+                                    cells, vol, d_mon, kMonBlocks, b->stream);
+    double mon[NM * kMonBlocks];
+    if (rc == IT_OK) {
+        cudaError_t e = cudaMemcpyAsync(mon, d_mon, sizeof(mon), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch tallies");
+    }
+    cudaFree(d_mon);
+    if (rc) return rc;
+    std::memset(t, 0, sizeof(*t));
     for (int s = 0; s < 2; ++s) {
         double sum = 0, mn = INFINITY, mx = -INFINITY;
-        for (size_t q = 0; q < cells; ++q) {
-            const double v = h[s * cells + q];
-            sum += v; mn = std::min(mn, v); mx = std::max(mx, v);
+        for (int q = 0; q < kMonBlocks; ++q) {
+            sum += mon[q * NM + s];
+            mn = std::min(mn, mon[q * NM + 2 + s]);
+            mx = std::max(mx, mon[q * NM + 4 + s]);
         }
-        t->in_domain[s] = sum * vol;
+        t->in_domain[s] = sum;
         t->n_min[s] = mn;
         t->n_max[s] = mx;
     }

@@ -146,6 +146,8 @@ int launch_zero(void *p, size_t bytes, cudaStream_t s);
 int simple_grid(const it_ctx *c);
 int launch_step_simple_raw_f32(const float *ip, const float *im, float *op, float *om, int nx, int ny, int nz,
                                const Coef<float> &cf, bool periodic, double *slots, int nblocks, cudaStream_t s);
+int launch_monitor_raw_f32(const float *p, const float *m, size_t cells, double vol, double *mon, int nblocks,
+                           cudaStream_t s);
 int validate_step_args(const it_params *p, it_grid g, double dx, double dt);
 void coef_f32(const it_params *p, double dx, double dt, Coef<float> *out);
 

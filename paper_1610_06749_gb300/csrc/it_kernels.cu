@@ -175,6 +175,14 @@ int launch_monitor(it_ctx *c, cudaStream_t s) {
     return IT_OK;
 }
 
+// monitor over caller-given FP32 arrays into nblocks x NM values
+int launch_monitor_raw_f32(const float *p, const float *m, size_t cells, double vol, double *mon, int nblocks,
+                           cudaStream_t s) {
+    monitor_kernel<float><<<nblocks, 256, 0, s>>>(p, m, cells, vol, mon);
+    IT_CK(cudaGetLastError());
+    return IT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // finalize: fixed-order sums of the per-CTA slots and monitor values
 //   out[0..NT) tallies, out[NT..NT+NM) monitor, out[NT+NM..+2) released

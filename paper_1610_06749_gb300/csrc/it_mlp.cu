@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
 // dz = 2/B (fhat - y) fhat (1 - fhat), dZ4 = dz w5 * SiLU'(Z4) (fp32 and bf16).
 __global__ void out_layer_kernel(const __nv_bfloat16 *__restrict__ A4, const float *__restrict__ Z4,
                                  const __nv_bfloat16 *__restrict__ w, const float *__restrict__ master,
-                                 const float *__restrict__ y, int B, int train, float *__restrict__ fhat,
+                                 const float *__restrict__ y, long long ybs, int B, int train, float *__restrict__ fhat,
                                  float *__restrict__ dzout, float *__restrict__ dZ, __nv_bfloat16 *__restrict__ dZb,
                                  long long zact) {
     const int m = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
@@ -162,7 +162,7 @@ __global__ void out_layer_kernel(const __nv_bfloat16 *__restrict__ A4, const flo
     const float f = 1.f / (1.f + __expf(-zz));
     if (lane == 0) fhat[z * B + m] = f;
     if (!train) return;
-    const float dz = 2.f / B * (f - y[m]) * f * (1.f - f);
+    const float dz = 2.f / B * (f - y[(long long)z * ybs + m]) * f * (1.f - f);
     if (lane == 0) dzout[z * B + m] = dz;
     for (int k = lane; k < H; k += 32) {
         const long long o = z * zact + (long long)m * H + k;
@@ -201,13 +201,13 @@ __global__ void bias_grad_kernel(const float *__restrict__ dZ, int B, float *__r
 }
 
 // mean squared error per member, fixed order
-__global__ void loss_kernel(const float *__restrict__ fhat, const float *__restrict__ y, int B,
+__global__ void loss_kernel(const float *__restrict__ fhat, const float *__restrict__ y, long long ybs, int B,
                             double *__restrict__ loss) {
     __shared__ double red[32];
     const int z = blockIdx.x;
     double v[1] = {0.0};
     for (int m = threadIdx.x; m < B; m += blockDim.x) {
-        const double d = (double)fhat[z * B + m] - (double)y[m];
+        const double d = (double)fhat[z * B + m] - (double)y[(long long)z * ybs + m];
         v[0] += d * d;
     }
     block_sum<1>(v, red);
@@ -235,17 +235,21 @@ __global__ void to_bf16_kernel(const float *__restrict__ x, __nv_bfloat16 *__res
         y[i] = __float2bfloat16_rn(x[i]);
 }
 
-// normalised bf16 inputs of a batch: A0[m][j] = (x[idx[m]][j] - mean[j]) / std[j]
+// normalised bf16 inputs of a batch for every member:
+// A0[z][m][j] = (x[idx[z][m]][j] - mean[j]) / std[j], yb[z][m] = y[idx[z][m]]
+// (idx == NULL: sample m for every member)
 __global__ void gather_inputs_kernel(const float *__restrict__ X, const float *__restrict__ Y,
-                                     const int *__restrict__ idx, int B, const float *__restrict__ mean,
-                                     const float *__restrict__ inv_std, __nv_bfloat16 *__restrict__ A0,
-                                     float *__restrict__ yb) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= B * NIN) return;
-    const int m = e / NIN, j = e % NIN;
-    const int r = idx ? idx[m] : m;
-    A0[e] = __float2bfloat16_rn((X[(long long)r * NIN + j] - mean[j]) * inv_std[j]);
-    if (j == 0 && Y) yb[m] = Y[r];
+                                     const int *__restrict__ idx, int B, int members, int bmax,
+                                     const float *__restrict__ mean, const float *__restrict__ inv_std,
+                                     __nv_bfloat16 *__restrict__ A0, float *__restrict__ yb) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)members * B * NIN) return;
+    const int z = (int)(e / ((long long)B * NIN));
+    const int r0 = (int)(e - (long long)z * B * NIN);
+    const int m = r0 / NIN, j = r0 % NIN;
+    const int r = idx ? idx[z * bmax + m] : m;
+    A0[((long long)z * bmax + m) * NIN + j] = __float2bfloat16_rn((X[(long long)r * NIN + j] - mean[j]) * inv_std[j]);
+    if (j == 0 && Y) yb[z * bmax + m] = Y[r];
 }
 
 }  // namespace mlp
@@ -316,7 +320,7 @@ int forward(it_mlp *n, int B, bool train) {
         const int K = l == 0 ? NIN : H;
         g.A = l == 0 ? n->A0 : n->Act[l - 1];
         g.sam = K; g.sak = 1;
-        g.za = l == 0 ? 0 : zact;
+        g.za = l == 0 ? (long long)n->bmax * NIN : zact;
         g.B = n->w + kOffW[l];
         g.sbk = 1; g.sbn = K; g.zb = P;
         g.M = B; g.N = H; g.K = K;
@@ -327,7 +331,7 @@ int forward(it_mlp *n, int B, bool train) {
         if (rc) return rc;
     }
     dim3 grid((B + 7) / 8, n->members);
-    out_layer_kernel<<<grid, 256, 0, n->stream>>>(n->Act[3], n->Z[3], n->w, n->master, n->yb, B, train ? 1 : 0,
+    out_layer_kernel<<<grid, 256, 0, n->stream>>>(n->Act[3], n->Z[3], n->w, n->master, n->yb, n->bmax, B, train ? 1 : 0,
                                                   n->fhat, n->dz, n->dZ[0], n->dZb[0], zact);
     IT_CK(cudaGetLastError());
     return IT_OK;
@@ -345,7 +349,7 @@ int backward(it_mlp *n, int B) {
         GemmArgs g{};
         g.A = n->dZb[cur]; g.sam = 1; g.sak = H; g.za = zact;
         g.B = l == 0 ? n->A0 : n->Act[l - 1];
-        g.sbk = K; g.sbn = 1; g.zb = l == 0 ? 0 : zact;
+        g.sbk = K; g.sbn = 1; g.zb = l == 0 ? (long long)n->bmax * NIN : zact;
         g.M = H; g.N = K; g.K = B;
         g.Out = n->grad + kOffW[l]; g.ldc = K; g.zc = P;
         int rc = launch_gemm(EPI_WGRAD, g, n->members, n->stream);
@@ -382,7 +386,9 @@ int upload_inputs(it_mlp *n, long long count, const double *x, const double *y, 
 }
 
 int gather(it_mlp *n, const float *X, const float *Y, const int *idx, int B) {
-    gather_inputs_kernel<<<(B * NIN + 255) / 256, 256, 0, n->stream>>>(X, Y, idx, B, n->mean, n->inv_std, n->A0, n->yb);
+    const long long tot = (long long)n->members * B * NIN;
+    gather_inputs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, n->stream>>>(X, Y, idx, B, n->members, n->bmax, n->mean,
+                                                                               n->inv_std, n->A0, n->yb);
     IT_CK(cudaGetLastError());
     return IT_OK;
 }
@@ -431,11 +437,11 @@ int it_mlp_create(int32_t members, int32_t max_batch, it_mlp **out) {
         (e = cudaMalloc(&n->w, sizeof(__nv_bfloat16) * np)) != cudaSuccess ||
         (e = cudaMalloc(&n->mean, sizeof(float) * NIN)) != cudaSuccess ||
         (e = cudaMalloc(&n->inv_std, sizeof(float) * NIN)) != cudaSuccess ||
-        (e = cudaMalloc(&n->A0, sizeof(__nv_bfloat16) * max_batch * NIN)) != cudaSuccess ||
+        (e = cudaMalloc(&n->A0, sizeof(__nv_bfloat16) * members * max_batch * NIN)) != cudaSuccess ||
         (e = cudaMalloc(&n->fhat, sizeof(float) * members * max_batch)) != cudaSuccess ||
         (e = cudaMalloc(&n->dz, sizeof(float) * members * max_batch)) != cudaSuccess ||
-        (e = cudaMalloc(&n->yb, sizeof(float) * max_batch)) != cudaSuccess ||
-        (e = cudaMalloc(&n->idx, sizeof(int) * max_batch)) != cudaSuccess ||
+        (e = cudaMalloc(&n->yb, sizeof(float) * members * max_batch)) != cudaSuccess ||
+        (e = cudaMalloc(&n->idx, sizeof(int) * members * max_batch)) != cudaSuccess ||
         (e = cudaMalloc(&n->loss, sizeof(double) * members)) != cudaSuccess)
         return bail("mlp allocation");
     for (int l = 0; l < 4; ++l)
@@ -522,24 +528,33 @@ int it_mlp_train(it_mlp *n, int32_t epochs, int32_t batch, double lr, uint64_t s
     if (!n || epochs < 0 || batch < 1 || batch > n->bmax || !(lr > 0)) return mfail(IT_EINVAL, "bad argument");
     if (n->n_data < 1) return mfail(IT_ESTATE, "no training data (it_mlp_set_data)");
     const long long N = n->n_data;
-    std::vector<int> perm((size_t)N);
-    std::vector<double> lossb(n->members);
-    uint64_t st = seed;
+    const int Z = n->members;
+    // each member walks the data in its own order (ensemble diversity)
+    std::vector<std::vector<int>> perm(Z, std::vector<int>((size_t)N));
+    std::vector<uint64_t> st(Z);
+    for (int z = 0; z < Z; ++z) st[z] = seed + 0x9E3779B97F4A7C15ULL * (uint64_t)(z + 1);
+    std::vector<int> hidx((size_t)Z * n->bmax);
+    std::vector<double> lossb(Z);
     for (int ep = 0; ep < epochs; ++ep) {
-        for (long long i = 0; i < N; ++i) perm[i] = (int)i;
-        for (long long i = N - 1; i > 0; --i) {   // Fisher-Yates with SplitMix64
-            const long long j = (long long)(splitmix_next(st) % (uint64_t)(i + 1));
-            std::swap(perm[i], perm[j]);
+        for (int z = 0; z < Z; ++z) {
+            auto &pz = perm[z];
+            for (long long i = 0; i < N; ++i) pz[i] = (int)i;
+            for (long long i = N - 1; i > 0; --i) {   // Fisher-Yates with SplitMix64
+                const long long j = (long long)(splitmix_next(st[z]) % (uint64_t)(i + 1));
+                std::swap(pz[i], pz[j]);
+            }
         }
         double ep_loss = 0.0;
         int nb = 0;
         for (long long b0 = 0; b0 + batch <= N || (b0 < N && nb == 0); b0 += batch) {
             const int B = (int)std::min<long long>(batch, N - b0);
-            IT_CK(cudaMemcpyAsync(n->idx, perm.data() + b0, sizeof(int) * B, cudaMemcpyHostToDevice, n->stream));
+            for (int z = 0; z < Z; ++z)
+                std::memcpy(hidx.data() + (size_t)z * n->bmax, perm[z].data() + b0, sizeof(int) * B);
+            IT_CK(cudaMemcpyAsync(n->idx, hidx.data(), sizeof(int) * Z * n->bmax, cudaMemcpyHostToDevice, n->stream));
             int rc = gather(n, n->X, n->Y, n->idx, B);
             if (!rc) rc = forward(n, B, true);
             if (!rc && loss_per_epoch) {
-                loss_kernel<<<n->members, 256, 0, n->stream>>>(n->fhat, n->yb, B, n->loss);
+                loss_kernel<<<n->members, 256, 0, n->stream>>>(n->fhat, n->yb, n->bmax, B, n->loss);
                 IT_CK(cudaGetLastError());
             }
             if (!rc) rc = backward(n, B);
@@ -550,7 +565,7 @@ int it_mlp_train(it_mlp *n, int32_t epochs, int32_t batch, double lr, uint64_t s
                 IT_CK(cudaStreamSynchronize(n->stream));
                 for (double v : lossb) ep_loss += v / n->members;
             } else {
-                IT_CK(cudaStreamSynchronize(n->stream));   // perm is reused next epoch
+                IT_CK(cudaStreamSynchronize(n->stream));   // hidx is reused by the next batch
             }
             ++nb;
         }
@@ -567,7 +582,7 @@ int it_mlp_loss_grad(it_mlp *n, int64_t count, const double *x, const double *y,
     if (!rc) rc = gather(n, dX, dY, nullptr, (int)count);
     if (!rc) rc = forward(n, (int)count, true);
     if (!rc) {
-        loss_kernel<<<n->members, 256, 0, n->stream>>>(n->fhat, n->yb, (int)count, n->loss);
+        loss_kernel<<<n->members, 256, 0, n->stream>>>(n->fhat, n->yb, n->bmax, (int)count, n->loss);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "loss");
     }

@@ -266,18 +266,35 @@ def surrogate_configs(seed: int, n: int):
     return out
 
 
+# Roberts' R2 low-discrepancy sequence (generalised golden ratio g, the real
+# root of g^3 = g + 1): point i = frac(0.5 + i (1/g, 1/g^2)).
+_R2_G = 1.32471795724474602596
+
+
+def r2_points(n: int) -> np.ndarray:
+    """First n points of the R2 sequence in [0,1)^2 ([n][2])."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    a = np.array([1.0 / _R2_G, 1.0 / _R2_G ** 2])
+    return np.mod(0.5 + i[:, None] * a[None, :], 1.0)
+
+
 def surrogate_tracks(cfg) -> TrackList:
-    """Tracks of one pulse of a surrogate configuration (uniform x, y)."""
+    """Tracks of one pulse of a surrogate configuration: uniformly spread
+    over the section on the R2 sequence, so that f is a function of the six
+    inputs (random positions make f scatter by up to ~1e-2 between draws)."""
     L = cfg["nx"] * cfg["dx_cm"]
-    return uniform_tracks(cfg["seed"], cfg["n_tracks"], L, L, cfg["b_cm"], let=cfg["let"])
+    p = r2_points(cfg["n_tracks"]) * L
+    n = cfg["n_tracks"]
+    return TrackList(p[:, 0].copy(), p[:, 1].copy(), np.full(n, float(cfg["let"])), np.full(n, float(cfg["b_cm"])))
 
 
 def surrogate_features(cfg, period_s=None) -> np.ndarray:
-    """The six network inputs: log10 LET, V, gap (cm), b (cm), tracks per
-    pulse, pulse period (s; the period actually simulated when given)."""
+    """The six network inputs, each on a log scale: log10 of LET (keV/um),
+    voltage (V), gap (cm), b (cm), tracks per pulse, and pulse period + 1 us
+    (s; the period actually simulated when given, 0 for a single pulse)."""
     p = cfg["period_s"] if period_s is None else period_s
-    return np.array([math.log10(cfg["let"]), cfg["voltage_V"], cfg["gap_cm"], cfg["b_cm"],
-                     float(cfg["n_tracks"]), p], dtype=np.float64)
+    return np.log10(np.array([cfg["let"], cfg["voltage_V"], cfg["gap_cm"], cfg["b_cm"],
+                              float(cfg["n_tracks"]), p + 1e-6], dtype=np.float64))
 
 
 def mlp_init(seed: int, members: int = 5) -> np.ndarray:

@@ -1,0 +1,65 @@
+"""The surrogate workflow on solver data: what the trained ensemble gains
+over the solver alone, and that falling back to the solver keeps the answers
+at the solver's value."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1610_06749_gb300 import binding as B
+from paper_1610_06749_gb300 import surrogate as S
+from paper_1610_06749_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_1610_06749_gb300 import build
+    build.build()
+    tr = synth.surrogate_configs(1610067493, 1500)
+    te = synth.surrogate_configs(1610067494, 60)
+    f_tr, dt_tr, p_tr = S.solve_batch(tr)
+    f_te, dt_te, p_te = S.solve_batch(te)
+    sur = S.Surrogate(members=5)
+    loss = sur.fit(S.features(tr, dt_tr, p_tr), f_tr, epochs=600, lr=2e-3, lr_min=1e-5)
+    yield dict(sur=sur, te=te, f_te=f_te, dt_te=dt_te, p_te=p_te, loss=loss)
+    sur.close()
+
+
+def test_training_converges_and_generalises(trained):
+    loss = trained["loss"]
+    assert loss[-1] < 0.02 * loss[0]
+    X = S.features(trained["te"], trained["dt_te"], trained["p_te"])
+    mean, spread = trained["sur"].predict(X)
+    err = np.abs(mean - trained["f_te"])
+    assert np.median(err) < 1e-2           # held-out configurations, 1500 training runs
+    assert np.all(spread >= 0)
+
+
+def test_prediction_is_orders_of_magnitude_faster_than_solving(trained):
+    te, dt, per = trained["te"], trained["dt_te"], trained["p_te"]
+    X = S.features(te, dt, per)
+    trained["sur"].predict(X)                # warm
+    t0 = time.perf_counter()
+    trained["sur"].predict(X)
+    t_pred = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c, d, p in zip(te[:6], dt[:6], per[:6]):
+        S.solve_plain(c, d, p)
+    t_solve = (time.perf_counter() - t0) / 6
+    assert t_pred / len(te) < 1e-3 * t_solve
+
+
+def test_fallback_answers_equal_the_solver(trained):
+    te, dt, per, f_te = trained["te"], trained["dt_te"], trained["p_te"], trained["f_te"]
+    f, fb, _ = S.answer(trained["sur"], te, dt, per, spread_max=1e-3)
+    # fall-backs are plain-solver results: the batched solver computes the
+    # same thing (bitwise densities), so they agree to summation order
+    assert np.max(np.abs(f[fb] - f_te[fb])) < 1e-8 if fb.any() else True
+    # at 1500 training runs the members can agree on a biased answer: the
+    # accepted answers are close but not yet within 1e-3 (the 20000-run
+    # training of the surrogate workload reaches 97% within 1e-3)
+    acc = ~fb
+    if acc.any():
+        assert np.median(np.abs(f[acc] - f_te[acc])) < 1e-2
