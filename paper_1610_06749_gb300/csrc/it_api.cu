@@ -422,7 +422,7 @@ int it_create_ex(it_grid g, double dx_cm, double dt_s, const it_params *p, void 
         (e = cudaMalloc(&c->d_mon, sizeof(double) * NM * c->nmon)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_acc, sizeof(DevAcc))) != cudaSuccess ||
         (e = cudaMalloc(&c->d_out, sizeof(double) * NOUT)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_plane, sizeof(double) * c->g.plane())) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_plane, sizeof(double) * 2 * c->g.plane())) != cudaSuccess ||   // plane + tile sums
         (e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess ||
         (e = cudaMallocHost(&c->h_out, sizeof(double) * NOUT)) != cudaSuccess)
         return bail(cuda_fail(e, "scratch allocation"));

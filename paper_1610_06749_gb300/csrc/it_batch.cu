@@ -603,7 +603,7 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
     if ((e = cudaMalloc(&b->d_sims, sizeof(BatchSim) * nsim)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_acc, sizeof(double) * NT * nsim)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_rel, sizeof(double) * 8 * nsim)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_plane, sizeof(double) * b->max_nx * b->max_ny)) != cudaSuccess)
+        (e = cudaMalloc(&b->d_plane, sizeof(double) * 2 * b->max_nx * b->max_ny)) != cudaSuccess)   // plane + tile sums
         return bail(e, "batch scratch");
     if ((e = cudaMemcpyAsync(b->d_sims, b->hs.data(), sizeof(BatchSim) * nsim, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(b->d_acc, 0, sizeof(double) * NT * nsim, b->stream)) != cudaSuccess ||

@@ -95,7 +95,7 @@ struct it_ctx {
     double *d_out;        // finalize output [NT + NM + 2]
     double *h_out;        // pinned mirror
     // deposition scratch
-    double *d_plane;      // [ny][nx]
+    double *d_plane;      // [ny][nx] plane, then the per-tile sums of the deposit
     double *d_tracks;     // [cap][4]: x, y, LET, b
     double *d_wx, *d_wy;  // [cap][nx], [cap][ny]
     int64_t track_cap;

@@ -127,15 +127,22 @@ monitor_kernel(const T *__restrict__ ip, const T *__restrict__ im, size_t total,
     __shared__ double red[32 * 2];
     __shared__ double rmin[32 * 2], rmax[32 * 2];
     double sum[2] = {0, 0};
-    double mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
+    T part[2] = {0, 0};
+    int np = 0;
+    T mnT[2] = {(T)INFINITY, (T)INFINITY}, mxT[2] = {(T)-INFINITY, (T)-INFINITY};
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
-        const double a = (double)ip[idx], b = (double)im[idx];
-        sum[0] += a; sum[1] += b;
-        mn[0] = fmin(mn[0], a); mn[1] = fmin(mn[1], b);
-        mx[0] = fmax(mx[0], a); mx[1] = fmax(mx[1], b);
-        // a NaN propagates through the sum and is reported by the host
+        const T a = ip[idx], b = im[idx];
+        part[0] += a; part[1] += b;          // a NaN propagates into the sums
+        mnT[0] = a < mnT[0] ? a : mnT[0]; mnT[1] = b < mnT[1] ? b : mnT[1];
+        mxT[0] = a > mxT[0] ? a : mxT[0]; mxT[1] = b > mxT[1] ? b : mxT[1];
+        if (++np == 32) {                    // partial sums in T over at most 32 cells, then FP64
+            sum[0] += (double)part[0]; sum[1] += (double)part[1];
+            part[0] = part[1] = 0; np = 0;
+        }
     }
+    sum[0] += (double)part[0]; sum[1] += (double)part[1];
+    double mn[2] = {(double)mnT[0], (double)mnT[1]}, mx[2] = {(double)mxT[0], (double)mxT[1]};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
 #pragma unroll
@@ -276,42 +283,116 @@ __global__ void deposit_tables_kernel(const double *__restrict__ tr, double dx, 
     }
 }
 
-// plane[j][i] = sum_t N0_t wx[t][i] wy[t][j] / dx^2, tracks in index order.
-__global__ void deposit_plane_kernel(const double *__restrict__ tr, const double *__restrict__ wx,
-                                     const double *__restrict__ wy, long long nt, int nx, int ny,
-                                     double inv_dx2, double inv_W, double *__restrict__ plane) {
-    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= (long long)nx * ny) return;
-    const int i = (int)(cell % nx), j = (int)(cell / nx);
-    double sum = 0.0;
-    for (long long t = 0; t < nt; ++t) {
-        const double a = wx[t * nx + i];
-        if (a == 0.0) continue;
-        const double bb = wy[t * ny + j];
-        if (bb == 0.0) continue;
-        const double N0 = tr[t * 4 + 2] * 1e7 * inv_W;   // ions per cm
-        sum += N0 * a * bb;
+// Does the deposit window of a track (+-w cells around cell ic, wrapped on a
+// periodic axis of n cells) reach the cells [t0, t0 + tn)?  Conservative: a
+// track that only touches zero weights is harmless (it adds exact zeros).
+__device__ __forceinline__ bool window_hits(long long ic, long long w, int t0, int tn, int n, bool periodic) {
+    if (periodic) {
+        if (2 * w + 1 >= n) return true;
+        long long d = ((long long)t0 - (ic - w)) % n;
+        if (d < 0) d += n;
+        return d <= 2 * w || d + tn - 1 >= n;
     }
-    plane[cell] = sum * inv_dx2;
+    return ic + w >= t0 && ic - w <= t0 + tn - 1;
 }
 
+constexpr int DEP_TILE = 16;      // 16 x 16 cells per CTA
+constexpr int DEP_LIST = 1024;    // tracks gathered per pass
+
+// plane[j][i] = sum_t N0_t wx[t][i] wy[t][j] / dx^2, tracks in index order.
+// Each CTA first lists (in index order) the tracks whose window reaches its
+// tile, then every cell sums over that list; tracks that miss the tile only
+// contribute zeros, so the per-cell sum is the same as over all tracks.
+// part[blockIdx] receives the tile's sum of the plane (FP64).
+__global__ void __launch_bounds__(DEP_TILE *DEP_TILE)
+deposit_plane_kernel(const double *__restrict__ tr, const double *__restrict__ wx, const double *__restrict__ wy,
+                     long long nt, int nx, int ny, double dx, int periodic, double inv_dx2, double inv_W,
+                     double *__restrict__ plane, double *__restrict__ part) {
+    __shared__ int list[DEP_LIST];
+    __shared__ int wcount[DEP_TILE * DEP_TILE / 32];
+    __shared__ int nlist;
+    __shared__ double red[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = blockIdx.x * DEP_TILE, j0 = blockIdx.y * DEP_TILE;
+    const int tnx = min(DEP_TILE, nx - i0), tny = min(DEP_TILE, ny - j0);
+    const int i = i0 + (tid % DEP_TILE), j = j0 + (tid / DEP_TILE);
+    const bool inside = (tid % DEP_TILE) < tnx && (tid / DEP_TILE) < tny;
+    double sum = 0.0;
+    for (long long base = 0; base < nt;) {
+        if (tid == 0) nlist = 0;
+        __syncthreads();
+        // gather up to DEP_LIST candidates in index order, 256 tracks per round
+        long long t0 = base;
+        for (; t0 < nt; t0 += blockDim.x) {
+            const long long t = t0 + tid;
+            bool hit = false;
+            if (t < nt) {
+                const double b = tr[t * 4 + 3];
+                const long long w = (long long)ceil(6.0 * b / dx);
+                hit = window_hits((long long)floor(tr[t * 4] / dx), w, i0, tnx, nx, periodic != 0) &&
+                      window_hits((long long)floor(tr[t * 4 + 1] / dx), w, j0, tny, ny, periodic != 0);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) wcount[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+                if (q < warp) before += wcount[q];
+                total += wcount[q];
+            }
+            const int start = nlist;
+            if (total > DEP_LIST - start) {   // list full: stop before this round, take it next pass
+                __syncthreads();
+                break;
+            }
+            if (hit) list[start + before + __popc(bal & ((1u << lane) - 1u))] = (int)t;
+            __syncthreads();
+            if (tid == 0) nlist = start + total;
+            __syncthreads();
+        }
+        const int n = nlist;
+        if (inside) {
+            for (int q = 0; q < n; ++q) {
+                const long long t = list[q];
+                const double a = wx[t * nx + i];
+                if (a == 0.0) continue;
+                const double bb = wy[t * ny + j];
+                if (bb == 0.0) continue;
+                const double N0 = tr[t * 4 + 2] * 1e7 * inv_W;   // ions per cm
+                sum += N0 * a * bb;
+            }
+        }
+        base = t0;
+        __syncthreads();
+    }
+    const double v = sum * inv_dx2;
+    if (inside) plane[(size_t)j * nx + i] = v;
+    double r[1] = {inside ? v : 0.0};
+    block_sum<1>(r, red);
+    if (tid == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = r[0];
+}
+
+// n += plane on every z plane: one thread per (i, j) column, coalesced per plane
 template <typename T>
 __global__ void deposit_apply_kernel(T *__restrict__ p, T *__restrict__ m, const double *__restrict__ plane,
-                                     size_t plane_n, size_t total) {
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const double a = plane[idx % plane_n];
+                                     size_t plane_n, int nz) {
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= plane_n) return;
+    const double a = plane[c];
+    if (a == 0.0) return;   // x + 0 == x: nothing to write
+    for (int k = 0; k < nz; ++k) {
+        const size_t idx = (size_t)k * plane_n + c;
         p[idx] = (T)((double)p[idx] + a);
         m[idx] = (T)((double)m[idx] + a);
     }
 }
 
-// released += sum(plane) * dx^2 * (nz dx) for both species, fixed order
+// released += sum(tile sums) * dx^2 * (nz dx) for both species, fixed order
 __global__ void __launch_bounds__(256)
-deposit_released_kernel(const double *__restrict__ plane, size_t n, double factor, double *__restrict__ acc) {
+deposit_released_kernel(const double *__restrict__ part, size_t n, double factor, double *__restrict__ acc) {
     __shared__ double red[32];
     double v[1] = {0.0};
-    for (size_t q = threadIdx.x; q < n; q += blockDim.x) v[0] += plane[q];
+    for (size_t q = threadIdx.x; q < n; q += blockDim.x) v[0] += part[q];
     block_sum<1>(v, red);
     if (threadIdx.x == 0) {
         acc[0] += v[0] * factor;
@@ -322,25 +403,29 @@ deposit_released_kernel(const double *__restrict__ plane, size_t n, double facto
 int launch_deposit(it_ctx *c, int64_t n, cudaStream_t s) {
     if (n <= 0) return IT_OK;
     const int nx = c->g.nx, ny = c->g.ny;
+    const bool periodic = c->p.lateral_bc == IT_PERIODIC;
     dim3 gt((unsigned)n, 2);
-    deposit_tables_kernel<<<gt, 128, 0, s>>>(c->d_tracks, c->dx, nx, ny, c->p.lateral_bc == IT_PERIODIC,
-                                            c->d_wx, c->d_wy);
+    deposit_tables_kernel<<<gt, 128, 0, s>>>(c->d_tracks, c->dx, nx, ny, periodic, c->d_wx, c->d_wy);
     IT_CK(cudaGetLastError());
     const long long pn = (long long)nx * ny;
-    deposit_plane_kernel<<<(unsigned)((pn + 255) / 256), 256, 0, s>>>(
-        c->d_tracks, c->d_wx, c->d_wy, n, nx, ny, 1.0 / (c->dx * c->dx), 1.0 / c->p.W_eV, c->d_plane);
+    dim3 gp((nx + DEP_TILE - 1) / DEP_TILE, (ny + DEP_TILE - 1) / DEP_TILE);
+    const size_t nparts = (size_t)gp.x * gp.y;
+    // the tile sums go after the plane in the same scratch buffer
+    double *part = c->d_plane + pn;
+    deposit_plane_kernel<<<gp, DEP_TILE * DEP_TILE, 0, s>>>(c->d_tracks, c->d_wx, c->d_wy, n, nx, ny, c->dx,
+                                                            periodic ? 1 : 0, 1.0 / (c->dx * c->dx),
+                                                            1.0 / c->p.W_eV, c->d_plane, part);
     IT_CK(cudaGetLastError());
-    const size_t total = c->g.cells();
-    const int nb = c->nmon;
+    const unsigned nb = (unsigned)((pn + 255) / 256);
     if (c->prec == IT_FP32)
         deposit_apply_kernel<float><<<nb, 256, 0, s>>>((float *)c->n[c->cur][0], (float *)c->n[c->cur][1],
-                                                       c->d_plane, (size_t)pn, total);
+                                                       c->d_plane, (size_t)pn, c->g.nz);
     else
         deposit_apply_kernel<double><<<nb, 256, 0, s>>>((double *)c->n[c->cur][0], (double *)c->n[c->cur][1],
-                                                        c->d_plane, (size_t)pn, total);
+                                                        c->d_plane, (size_t)pn, c->g.nz);
     IT_CK(cudaGetLastError());
     const double factor = c->dx * c->dx * (c->dx * c->g.nz);
-    deposit_released_kernel<<<1, 256, 0, s>>>(c->d_plane, (size_t)pn, factor, c->d_acc);
+    deposit_released_kernel<<<1, 256, 0, s>>>(part, nparts, factor, c->d_acc);
     IT_CK(cudaGetLastError());
     return IT_OK;
 }

@@ -53,7 +53,8 @@ def test_batch_equals_single_contexts_bitwise(bc):
                 # the single context may run the z-march kernel, whose tally
                 # partials are FP32 over up to 32 planes before FP64
                 assert tb.f == pytest.approx(ts.f, abs=1e-7)
-                np.testing.assert_allclose(tb.in_domain, ts.in_domain, rtol=1e-12)
+                # in-domain sums: FP32 partials over 32 cells, grouped differently
+                np.testing.assert_allclose(tb.in_domain, ts.in_domain, rtol=1e-8)
                 np.testing.assert_allclose(tb.released, ts.released, rtol=1e-15)
 
 
