@@ -146,6 +146,30 @@ struct Producer {
     uint32_t issued;
 };
 
+// Four cells of upd7 (one float4 x-segment) with paired FP32 operations:
+// each lane of a paired operation rounds exactly like the scalar operation,
+// and the sequence is the one of upd7, so the results are bitwise those of
+// the scalar kernels.
+__device__ __forceinline__ float4 upd7x4(float4 n, float l, float r, float4 u, float4 d, float4 zm, float4 zp,
+                                         float2 rxy, float2 rzw, float w0, float wx, float wy, float wzm, float wzp,
+                                         float adt) {
+    const float2 W0 = make_float2(w0, w0), WX = make_float2(wx, wx), WY = make_float2(wy, wy);
+    const float2 WZM = make_float2(wzm, wzm), WZP = make_float2(wzp, wzp), NA = make_float2(-adt, -adt);
+    float2 a = __fmul2_rn(W0, make_float2(n.x, n.y));
+    float2 b = __fmul2_rn(W0, make_float2(n.z, n.w));
+    a = __ffma2_rn(WX, make_float2(l + n.y, n.x + n.z), a);
+    b = __ffma2_rn(WX, make_float2(n.y + n.w, n.z + r), b);
+    a = __ffma2_rn(WY, __fadd2_rn(make_float2(u.x, u.y), make_float2(d.x, d.y)), a);
+    b = __ffma2_rn(WY, __fadd2_rn(make_float2(u.z, u.w), make_float2(d.z, d.w)), b);
+    a = __ffma2_rn(WZM, make_float2(zm.x, zm.y), a);
+    b = __ffma2_rn(WZM, make_float2(zm.z, zm.w), b);
+    a = __ffma2_rn(WZP, make_float2(zp.x, zp.y), a);
+    b = __ffma2_rn(WZP, make_float2(zp.z, zp.w), b);
+    a = __ffma2_rn(NA, rxy, a);
+    b = __ffma2_rn(NA, rzw, b);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
 // Warp-specialised-by-lane persistent step kernel (NW warps, all consumers).
 //   Lane 0 of warp 0 also streams the planes this CTA needs into an S-deep
 //   ring with TMA ("pump", non-blocking): full[slot] completes when a plane's
@@ -153,7 +177,9 @@ struct Producer {
 //   pumping while it waits for data, so a plane is always issued before
 //   anyone needs it.
 //   Every warp marches up z, one plane per iteration, with no block-wide
-//   barrier inside the march.
+//   barrier inside the march.  Register budget: the producer state and the
+//   FP64 tallies live in shared memory (each warp's lane 0 adds to its own
+//   tally row), so the registers hold only the marching planes and offsets.
 template <bool PERIODIC, int IPT, int NW>
 __global__ void __launch_bounds__(NW * 32, (NW <= 8 ? 2 : 1))
 step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp, float *__restrict__ outm,
@@ -166,7 +192,8 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     float *ring = reinterpret_cast<float *>(smem_base);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_base + (size_t)zc.S * zc.slot * sizeof(float));
     uint64_t *empty = full + zc.S;
-    __shared__ double red[32 * 7];
+    __shared__ double wacc[NW * 8];      // per-warp FP64 tallies (tally q of warp w at w*8+q)
+    __shared__ Producer pr;              // producer state, touched by thread 0 only
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
@@ -178,27 +205,25 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     const long long total = (long long)zc.ntile * nz;
     const long long g0 = total * blockIdx.x / gridDim.x;
     const long long g1 = total * (blockIdx.x + 1) / gridDim.x;
+    const bool is_producer = tid == 0;
 
-    if (tid == 0) {
+    if (is_producer) {
         for (int q = 0; q < S; ++q) {
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], NW);
         }
+        for (int q = 0; q < NW * 8; ++q) wacc[q] = 0.0;
         abort_flag = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    const bool is_producer = tid == 0;
-    Producer pr;
-    if (is_producer) {
         pr.seg = Segs{g0, g1, nz, 0, 0, 0};
         pr.live = pr.seg.next();
         pr.p = pr.live ? pr.seg.lo() : 0;
         pr.pos = RingPos{0, 0u};
         pr.issued = 0;
+        fence_mbar_init();
     }
-    // issue as many planes as free slots allow (lane 0 of warp 0 only)
+    __syncthreads();
+
+    // issue as many planes as free slots allow (thread 0 only)
     auto pump = [&]() {
         while (pr.live) {
             if (pr.issued >= (uint32_t)S && !mbar_test_wait(&empty[pr.pos.slot], pr.pos.phase ^ 1u)) return;
@@ -210,30 +235,42 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
             const uint32_t tx = 2u * zc.nbx * (uint32_t)(zc.TY + has_top + has_bot) * zc.bx * 4u;
             float *base = ring + (size_t)pr.pos.slot * zc.slot;
             uint64_t *bar = &full[pr.pos.slot];
+            const int p = pr.p;
             fence_proxy_async();
             mbar_arrive_expect_tx(bar, tx);
             for (int s = 0; s < 2; ++s) {
                 for (int b = 0; b < zc.nbx; ++b) {
                     float *blk = base + (size_t)(s * zc.nbx + b) * zc.blk;
-                    tma_load3(blk + zc.reg_main, &maps.main[s], bar, b * zc.bx, y0, pr.p);
-                    if (has_top) tma_load3(blk + zc.reg_top, &maps.halo[s], bar, b * zc.bx, ytop, pr.p);
-                    if (has_bot) tma_load3(blk + zc.reg_bot, &maps.halo[s], bar, b * zc.bx, ybot, pr.p);
+                    tma_load3(blk + zc.reg_main, &maps.main[s], bar, b * zc.bx, y0, p);
+                    if (has_top) tma_load3(blk + zc.reg_top, &maps.halo[s], bar, b * zc.bx, ytop, p);
+                    if (has_bot) tma_load3(blk + zc.reg_bot, &maps.halo[s], bar, b * zc.bx, ybot, p);
                 }
             }
             ++pr.issued;
             pr.pos.advance(S);
-            if (++pr.p > pr.seg.hi()) {
+            if (p + 1 > pr.seg.hi()) {
                 pr.live = pr.seg.next();
                 if (pr.live) pr.p = pr.seg.lo();
+            } else {
+                pr.p = p + 1;
             }
         }
     };
 
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    // warp-uniform: reduce one FP32 partial per lane in FP64 (fixed shuffle
+    // order) and add it to the warp's tally q
+    auto flush = [&](int q, float part) {
+        double v = (double)part;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) wacc[warp * 8 + q] += v;
+    };
 
-    // per-item offsets inside a species block (species 1: + nbx*blk)
+    // per-item offsets inside a species block (species 1: + nbx*blk); x
+    // neighbours are read from shared memory at wrapped offsets (periodic) or
+    // replaced by zero at an absorbing row end
     int o_c[IPT], o_u[IPT], o_d[IPT], o_l[IPT], o_r[IPT], ty_[IPT], c4_[IPT];
-    bool valid[IPT], need_l[IPT], need_r[IPT], zero_l[IPT], zero_r[IPT];
+    bool valid[IPT];
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
         const int q = tid + it * NT_;
@@ -248,22 +285,13 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         o_c[it] = bofs + zc.reg_main + ty * zc.bx + xi;
         o_u[it] = bofs + (ty == 0 ? zc.reg_top : zc.reg_main + (ty - 1) * zc.bx) + xi;
         o_d[it] = bofs + (ty == zc.TY - 1 ? zc.reg_bot : zc.reg_main + (ty + 1) * zc.bx) + xi;
-        // x neighbours come by shuffle from the adjacent lane, except where
-        // that lane is outside the warp or the row: then one scalar is read
-        // from shared memory (wrapped at a periodic row end, zero at an
-        // absorbing one)
-        const bool row_start = c4 == 0, row_end = c4 == ncol4 - 1;
-        need_l[it] = lane == 0 || row_start;
-        need_r[it] = lane == 31 || row_end;
-        zero_l[it] = !PERIODIC && row_start;
-        zero_r[it] = !PERIODIC && row_end;
-        const int xl = row_start ? nx - 1 : x0 - 1;
-        const int xr = row_end ? 0 : x0 + 4;
+        const int xl = c4 == 0 ? nx - 1 : x0 - 1;
+        const int xr = c4 == ncol4 - 1 ? 0 : x0 + 4;
         o_l[it] = (xl / zc.bx) * zc.blk + zc.reg_main + ty * zc.bx + (xl % zc.bx);
         o_r[it] = (xr / zc.bx) * zc.blk + zc.reg_main + ty * zc.bx + (xr % zc.bx);
     }
     const int sp_ofs = zc.nbx * zc.blk;
-    const size_t plane = (size_t)nx * ny;
+    const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     RingPos pos{0, 0u};
     bool failed = false;
@@ -272,7 +300,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     // A lost wait (about 2^32 cycles) marks the whole warp failed, so
     // shuffles stay convergent.
     auto wait_full = [&](const RingPos &u) {
-        if (warp == 0 && is_producer) pump();
+        if (is_producer) pump();
         bool ok = failed ? false : mbar_test_wait(&full[u.slot], u.phase);
         if (!__all_sync(0xffffffffu, ok) && !failed) {
             const long long t0 = clock64();
@@ -295,12 +323,12 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         const int za = seg.za, zb = seg.zb;
         const int y0 = seg.t * zc.TY;
         float4 prev[IPT][2], cur[IPT][2];
-        size_t off[IPT];
+        uint32_t off[IPT];       // element offset of the item in the current plane (cells < 2^32)
         bool zero_u[IPT], zero_d[IPT];
 #pragma unroll
         for (int it = 0; it < IPT; ++it) {
             const int yg = y0 + ty_[it];
-            off[it] = ((size_t)za * ny + yg) * nx + 4 * c4_[it];
+            off[it] = ((uint32_t)za * (uint32_t)ny + (uint32_t)yg) * (uint32_t)nx + 4u * (uint32_t)c4_[it];
             zero_u[it] = !PERIODIC && yg == 0;
             zero_d[it] = !PERIODIC && yg == ny - 1;
         }
@@ -329,10 +357,13 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                 cur[it][1] = *reinterpret_cast<const float4 *>(sl + sp_ofs + o_c[it]);
             }
         }
-        float rsum = 0.f;
+        float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f;
         int nacc = 0;
+        // not unrolled: an unrolled march (which would save the register
+        // rotation of prev/cur) measured slower
         for (int k = za; k < zb; ++k) {
             const bool has_next = k + 1 < nz;
+            const bool electrode = k == 0 || k == nz - 1;
             if (has_next) wait_full(pos);
             const float *sk = ring + (size_t)pc.slot * zc.slot;
             const float *sn = ring + (size_t)pos.slot * zc.slot;
@@ -340,7 +371,8 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
 #pragma unroll
             for (int it = 0; it < IPT; ++it) {
                 const float4 P = cur[it][0], M = cur[it][1];
-                const float4 rr = make_float4(P.x * M.x, P.y * M.y, P.z * M.z, P.w * M.w);
+                const float2 rxy = __fmul2_rn(make_float2(P.x, P.y), make_float2(M.x, M.y));
+                const float2 rzw = __fmul2_rn(make_float2(P.z, P.w), make_float2(M.z, M.w));
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const float *bk = sk + s * sp_ofs;
@@ -348,23 +380,19 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                     float4 u = *reinterpret_cast<const float4 *>(bk + o_u[it]);
                     float4 d = *reinterpret_cast<const float4 *>(bk + o_d[it]);
                     const float4 zp = has_next ? *reinterpret_cast<const float4 *>(sn + s * sp_ofs + o_c[it]) : zero4;
-                    if (zero_u[it]) u = zero4;
-                    if (zero_d[it]) d = zero4;
-                    float l = __shfl_up_sync(0xffffffffu, n.w, 1);
-                    float r = __shfl_down_sync(0xffffffffu, n.x, 1);
-                    if (need_l[it]) l = zero_l[it] ? 0.f : bk[o_l[it]];
-                    if (need_r[it]) r = zero_r[it] ? 0.f : bk[o_r[it]];
-                    const float4 zm = prev[it][s];
-                    const float w0 = cf.w0[s], wx = cf.wx[s], wy = cf.wy[s], wzm = cf.wzm[s], wzp = cf.wzp[s];
-                    const float adt = cf.adt;
-                    float4 v;
-                    v.x = upd7(n.x, l, n.y, u.x, d.x, zm.x, zp.x, rr.x, w0, wx, wy, wzm, wzp, adt);
-                    v.y = upd7(n.y, n.x, n.z, u.y, d.y, zm.y, zp.y, rr.y, w0, wx, wy, wzm, wzp, adt);
-                    v.z = upd7(n.z, n.y, n.w, u.z, d.z, zm.z, zp.z, rr.z, w0, wx, wy, wzm, wzp, adt);
-                    v.w = upd7(n.w, n.z, r, u.w, d.w, zm.w, zp.w, rr.w, w0, wx, wy, wzm, wzp, adt);
+                    float l = bk[o_l[it]];
+                    float r = bk[o_r[it]];
+                    if (!PERIODIC) {
+                        if (zero_u[it]) u = zero4;
+                        if (zero_d[it]) d = zero4;
+                        if (c4_[it] == 0) l = 0.f;
+                        if (c4_[it] == ncol4 - 1) r = 0.f;
+                    }
+                    const float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
+                                            cf.wzm[s], cf.wzp[s], cf.adt);
                     if (valid[it] && !failed) {
                         *reinterpret_cast<float4 *>((s ? outm : outp) + off[it]) = v;
-                        if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
+                        if (electrode) an[s] += (n.x + n.y) + (n.z + n.w);
                         if (!PERIODIC) {
                             if (c4_[it] == 0) lat[s] += n.x;
                             if (c4_[it] == ncol4 - 1) lat[s] += n.w;
@@ -375,22 +403,24 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                     prev[it][s] = n;
                     cur[it][s] = zp;
                 }
-                if (valid[it]) rsum += (rr.x + rr.y) + (rr.z + rr.w);
+                if (valid[it]) rsum += (rxy.x + rxy.y) + (rzw.x + rzw.y);
                 off[it] += plane;
             }
             // FP32 partial sums over at most 32 planes, then FP64
-            if (++nacc == 32) { acc[0] += (double)rsum; rsum = 0.f; nacc = 0; }
-            if (k == 0) { acc[1] += (double)an[0]; acc[2] += (double)an[1]; }
-            if (k == nz - 1) { acc[3] += (double)an[0]; acc[4] += (double)an[1]; }
-            if (!PERIODIC) {
-                // lateral faces: x and y weights are equal for dx = dy (latx_f == laty_f)
-                acc[5] += (double)lat[0] * cf.latx_f[0];
-                acc[6] += (double)lat[1] * cf.latx_f[1];
+            if (!PERIODIC) { lsum0 += lat[0]; lsum1 += lat[1]; }
+            if (++nacc == 32) {
+                flush(0, rsum);
+                rsum = 0.f;
+                if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); lsum0 = lsum1 = 0.f; }
+                nacc = 0;
             }
+            if (k == 0) { flush(1, an[0]); flush(2, an[1]); }
+            if (k == nz - 1) { flush(3, an[0]); flush(4, an[1]); }
             release(pc);
             if (has_next) { pc = pos; pos.advance(S); }
         }
-        acc[0] += (double)rsum;
+        flush(0, rsum);
+        if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); }
         if (zb < nz) release(pc);   // the z1 halo plane of this segment
         if (failed) break;
     }
@@ -407,16 +437,23 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
             (void)mbar_wait_bounded(&full[j], ph);
         }
     }
-    block_sum<7>(acc, red);
+    __syncthreads();
     if (tid == 0 && !abort_flag) {
+        double acc[7];
+        for (int q = 0; q < 7; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < NW; ++w) t += wacc[w * 8 + q];
+            acc[q] = t;
+        }
         double *sl = slots + (size_t)blockIdx.x * NT;
         sl[0] += acc[0] * cf.rec_f;
         sl[1] += acc[1] * cf.anode_f[0];
         sl[2] += acc[2] * cf.anode_f[1];
         sl[3] += acc[3] * cf.cathode_f[0];
         sl[4] += acc[4] * cf.cathode_f[1];
-        sl[5] += acc[5];
-        sl[6] += acc[6];
+        // lateral faces: x and y weights are equal for dx = dy (latx_f == laty_f)
+        sl[5] += acc[5] * cf.latx_f[0];
+        sl[6] += acc[6] * cf.latx_f[1];
     }
 }
 
@@ -498,6 +535,10 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid
     if (c->prec != IT_FP32) { set_error("z-march kernel needs FP32 densities"); return IT_EINVAL; }
     if (nx % 4 != 0) { set_error("z-march kernel needs nx % 4 == 0"); return IT_EINVAL; }
     if (nx > 256 && nx % 256 != 0) { set_error("z-march kernel needs nx <= 256 or nx % 256 == 0"); return IT_EINVAL; }
+    if ((unsigned long long)nx * ny * nz > 0xFFFFFFFFull) {
+        set_error("z-march kernel indexes a species array with 32 bits: needs nx*ny*nz < 2^32");
+        return IT_EINVAL;
+    }
     const int cps = want_cps > 0 ? want_cps : 1;
     if (cps > 2) { set_error("z-march kernel runs 1 or 2 CTAs per SM"); return IT_EINVAL; }
     const int nw = cps == 1 ? 16 : 8;
