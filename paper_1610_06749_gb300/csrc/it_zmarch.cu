@@ -10,17 +10,21 @@
 //     up a chunk of z planes [z0, z1);
 //   * every plane it needs (z0-1 .. z1) arrives in a shared-memory slot by TMA
 //     (cp.async.bulk.tensor, 3-D tiles of n+ and n-): TY main rows plus one
-//     halo row above and below (wrapped when the lateral faces are periodic,
-//     left at zero when they absorb); an S-deep ring of slots keeps S-2 planes
-//     in flight while one plane is computed;
+//     halo row above and below, wrapped when the lateral faces are periodic.
+//     Rows and planes outside the tensor (the absorbing faces' ghost rows, the
+//     electrode ghost planes z = -1 and z = nz) are filled with zeros by TMA,
+//     which is exactly the boundary condition n = 0;
+//   * an S-deep ring of slots keeps S-2 planes in flight while one plane is
+//     computed; the last warp to finish reading a slot refills it;
 //   * each thread owns float4 x-segments and keeps their k-1 and k values in
-//     registers; x neighbours come from warp shuffles, y neighbours and the
-//     k+1 plane from shared memory;
+//     registers; x and y neighbours and the k+1 plane come from shared memory;
+//     the update runs on paired FP32 instructions (two cells per instruction);
 //   * results are stored with coalesced 16-byte stores; per-thread FP32
-//     partial sums per plane are accumulated in FP64 and reduced per CTA into
-//     the CTA's own tally slot (deterministic).
+//     partial sums (at most 32 planes) are reduced per warp in FP64 and per
+//     CTA into the CTA's own tally slot (deterministic).
 // Every mbarrier wait is bounded: a wait that runs out raises the device
-// error flag, waits (bounded) for the CTA's outstanding copies and returns.
+// error flag, and the CTA waits (bounded) for its outstanding copies and
+// returns.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -119,7 +123,8 @@ struct RingPos {
 // The CTA's work: tile-planes (y-tile t, plane z) in the order t*nz + z,
 // split into gridDim.x equal contiguous ranges.  A range is walked as
 // segments (one tile column each); a segment computing planes [za, zb) loads
-// planes max(za-1,0) .. min(zb, nz-1).
+// planes za-1 .. zb.  The electrode ghost planes z = -1 and z = nz lie
+// outside the tensor, and TMA fills them with zeros (n = 0 at the electrodes).
 struct Segs {
     long long L, g1;
     int nz;
@@ -132,19 +137,38 @@ struct Segs {
         L += zb - za;
         return true;
     }
-    __device__ __forceinline__ int lo() const { return za > 0 ? za - 1 : 0; }
-    __device__ __forceinline__ int hi() const { return zb < nz ? zb : nz - 1; }
+    __device__ __forceinline__ int lo() const { return za - 1; }
+    __device__ __forceinline__ int hi() const { return zb; }
 };
 
-// Producer state (lane 0 of warp 0): walks the same segments as the
-// consumers and issues one plane per ring slot.
-struct Producer {
-    Segs seg;
-    int p;            // next plane of the current segment to issue
-    bool live;        // a plane remains to be issued
-    RingPos pos;
-    uint32_t issued;
-};
+// Plane n of a CTA's load sequence: its segments in order, each loading
+// planes za-1 .. zb of its tile.  Returns false past the end.
+__device__ __forceinline__ bool plane_of(long long g0, long long g1, int nz, int n, int &t, int &z) {
+    long long L = g0;
+    while (L < g1) {
+        const int tt = (int)(L / nz);
+        const int za = (int)(L - (long long)tt * nz);
+        const int zb = (int)min((long long)nz, za + (g1 - L));
+        const int cnt = zb - za + 2;
+        if (n < cnt) {
+            t = tt;
+            z = za - 1 + n;
+            return true;
+        }
+        n -= cnt;
+        L += zb - za;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "r"(smem_u32(p)), "r"(v)
+                 : "memory");
+    return old;
+}
 
 // Four cells of upd7 (one float4 x-segment) with paired FP32 operations:
 // each lane of a paired operation rounds exactly like the scalar operation,
@@ -170,16 +194,18 @@ __device__ __forceinline__ float4 upd7x4(float4 n, float l, float r, float4 u, f
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// Warp-specialised-by-lane persistent step kernel (NW warps, all consumers).
-//   Lane 0 of warp 0 also streams the planes this CTA needs into an S-deep
-//   ring with TMA ("pump", non-blocking): full[slot] completes when a plane's
-//   bytes land, empty[slot] when all NW warps have released it.  Warp 0 keeps
-//   pumping while it waits for data, so a plane is always issued before
-//   anyone needs it.
+// Persistent step kernel: NW warps, all of them compute.
+//   The planes a CTA needs stream through an S-deep ring of shared-memory
+//   slots by TMA.  full[slot] completes when a plane's bytes have landed.
+//   There is no producer warp: every warp, after its reads of a slot, adds
+//   one to the slot's release counter, and the warp whose release completes
+//   the count (the last reader) refills the slot with the plane S further
+//   on.  So a slot is refilled the moment it is free, and all warps do the
+//   same work.
 //   Every warp marches up z, one plane per iteration, with no block-wide
-//   barrier inside the march.  Register budget: the producer state and the
-//   FP64 tallies live in shared memory (each warp's lane 0 adds to its own
-//   tally row), so the registers hold only the marching planes and offsets.
+//   barrier inside the march.  The FP64 tallies live in shared memory (each
+//   warp's lane 0 adds to its own row), so the registers hold only the
+//   marching planes and offsets.
 template <bool PERIODIC, int IPT, int NW>
 __global__ void __launch_bounds__(NW * 32, (NW <= 8 ? 2 : 1))
 step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp, float *__restrict__ outm,
@@ -191,9 +217,9 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     unsigned char *smem_base = zm_smem_raw + ((128u - (smem_u32(zm_smem_raw) & 127u)) & 127u);
     float *ring = reinterpret_cast<float *>(smem_base);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_base + (size_t)zc.S * zc.slot * sizeof(float));
-    uint64_t *empty = full + zc.S;
+    uint32_t *rel = reinterpret_cast<uint32_t *>(full + zc.S);   // release counters
+    uint32_t *fills = rel + zc.S;                                  // loads issued per slot
     __shared__ double wacc[NW * 8];      // per-warp FP64 tallies (tally q of warp w at w*8+q)
-    __shared__ Producer pr;              // producer state, touched by thread 0 only
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
@@ -205,57 +231,53 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     const long long total = (long long)zc.ntile * nz;
     const long long g0 = total * blockIdx.x / gridDim.x;
     const long long g1 = total * (blockIdx.x + 1) / gridDim.x;
-    const bool is_producer = tid == 0;
 
-    if (is_producer) {
+    // planes this CTA loads: every segment [za, zb) loads zb - za + 2
+    int nload = 0;
+    {
+        Segs sg{g0, g1, nz, 0, 0, 0};
+        while (sg.next()) nload += sg.zb - sg.za + 2;
+    }
+
+    // load plane n of the sequence into its slot (one thread)
+    auto issue = [&](int n) {
+        int t = 0, p = 0;
+        if (!plane_of(g0, g1, nz, n, t, p)) return;
+        const int slot = n % S;
+        const int y0 = t * zc.TY;
+        // halo rows: wrapped when periodic; rows -1 and ny otherwise, which
+        // lie outside the tensor and arrive as zeros (absorbing faces hold
+        // n = 0); planes -1 and nz arrive as zeros the same way
+        const int ytop = PERIODIC ? (y0 > 0 ? y0 - 1 : ny - 1) : y0 - 1;
+        const int ybot = PERIODIC ? (y0 + zc.TY < ny ? y0 + zc.TY : 0) : y0 + zc.TY;
+        const uint32_t tx = 2u * zc.nbx * (uint32_t)(zc.TY + 2) * zc.bx * 4u;
+        float *base = ring + (size_t)slot * zc.slot;
+        uint64_t *bar = &full[slot];
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, tx);
+        for (int s = 0; s < 2; ++s) {
+            for (int b = 0; b < zc.nbx; ++b) {
+                float *blk = base + (size_t)(s * zc.nbx + b) * zc.blk;
+                tma_load3(blk + zc.reg_main, &maps.main[s], bar, b * zc.bx, y0, p);
+                tma_load3(blk + zc.reg_top, &maps.halo[s], bar, b * zc.bx, ytop, p);
+                tma_load3(blk + zc.reg_bot, &maps.halo[s], bar, b * zc.bx, ybot, p);
+            }
+        }
+        fills[slot] += 1;
+    };
+
+    if (tid == 0) {
         for (int q = 0; q < S; ++q) {
             mbar_init(&full[q], 1);
-            mbar_init(&empty[q], NW);
+            rel[q] = 0;
+            fills[q] = 0;
         }
         for (int q = 0; q < NW * 8; ++q) wacc[q] = 0.0;
         abort_flag = 0;
-        pr.seg = Segs{g0, g1, nz, 0, 0, 0};
-        pr.live = pr.seg.next();
-        pr.p = pr.live ? pr.seg.lo() : 0;
-        pr.pos = RingPos{0, 0u};
-        pr.issued = 0;
         fence_mbar_init();
+        for (int n = 0; n < S && n < nload; ++n) issue(n);
     }
     __syncthreads();
-
-    // issue as many planes as free slots allow (thread 0 only)
-    auto pump = [&]() {
-        while (pr.live) {
-            if (pr.issued >= (uint32_t)S && !mbar_test_wait(&empty[pr.pos.slot], pr.pos.phase ^ 1u)) return;
-            const int y0 = pr.seg.t * zc.TY;
-            const bool has_top = PERIODIC || y0 > 0;
-            const bool has_bot = PERIODIC || y0 + zc.TY < ny;
-            const int ytop = y0 > 0 ? y0 - 1 : ny - 1;
-            const int ybot = y0 + zc.TY < ny ? y0 + zc.TY : 0;
-            const uint32_t tx = 2u * zc.nbx * (uint32_t)(zc.TY + has_top + has_bot) * zc.bx * 4u;
-            float *base = ring + (size_t)pr.pos.slot * zc.slot;
-            uint64_t *bar = &full[pr.pos.slot];
-            const int p = pr.p;
-            fence_proxy_async();
-            mbar_arrive_expect_tx(bar, tx);
-            for (int s = 0; s < 2; ++s) {
-                for (int b = 0; b < zc.nbx; ++b) {
-                    float *blk = base + (size_t)(s * zc.nbx + b) * zc.blk;
-                    tma_load3(blk + zc.reg_main, &maps.main[s], bar, b * zc.bx, y0, p);
-                    if (has_top) tma_load3(blk + zc.reg_top, &maps.halo[s], bar, b * zc.bx, ytop, p);
-                    if (has_bot) tma_load3(blk + zc.reg_bot, &maps.halo[s], bar, b * zc.bx, ybot, p);
-                }
-            }
-            ++pr.issued;
-            pr.pos.advance(S);
-            if (p + 1 > pr.seg.hi()) {
-                pr.live = pr.seg.next();
-                if (pr.live) pr.p = pr.seg.lo();
-            } else {
-                pr.p = p + 1;
-            }
-        }
-    };
 
     // warp-uniform: reduce one FP32 partial per lane in FP64 (fixed shuffle
     // order) and add it to the warp's tally q
@@ -292,30 +314,36 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     }
     const int sp_ofs = zc.nbx * zc.blk;
     const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     RingPos pos{0, 0u};
+    int nrel = 0;            // planes of the sequence this warp has released
     bool failed = false;
 
-    // Wait for the plane at ring position u.  Warp 0 pumps while it waits.
-    // A lost wait (about 2^32 cycles) marks the whole warp failed, so
-    // shuffles stay convergent.
+    // Wait (bounded, about 2^32 cycles) for the plane at ring position u.  A
+    // lost wait marks the whole warp failed (shuffles stay convergent) and
+    // raises the CTA's abort flag, after which no warp waits again.
     auto wait_full = [&](const RingPos &u) {
-        if (is_producer) pump();
-        bool ok = failed ? false : mbar_test_wait(&full[u.slot], u.phase);
-        if (!__all_sync(0xffffffffu, ok) && !failed) {
-            const long long t0 = clock64();
-            for (;;) {
-                if (is_producer) pump();
-                ok = ok || mbar_try_wait(&full[u.slot], u.phase);
-                if (__all_sync(0xffffffffu, ok)) break;
-                if (abort_flag || clock64() - t0 > (1LL << 32)) { ok = false; break; }
-            }
+        if (failed) return;
+        bool ok = mbar_try_wait(&full[u.slot], u.phase);
+        if (__all_sync(0xffffffffu, ok)) return;
+        const long long t0 = clock64();
+        for (;;) {
+            ok = ok || mbar_try_wait(&full[u.slot], u.phase);
+            if (__all_sync(0xffffffffu, ok)) return;
+            if (__any_sync(0xffffffffu, abort_flag || clock64() - t0 > (1LL << 32))) break;
         }
-        failed = __any_sync(0xffffffffu, !ok);
+        failed = true;
+        if (lane == 0) abort_flag = 1;
     };
+    // After the warp's reads of the slot: count the release; the last of the
+    // NW releases refills the slot.  A failed warp releases nothing, so no
+    // slot is refilled while its previous load may still be in flight.
     auto release = [&](const RingPos &u) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[u.slot]);
+        if (lane == 0 && !failed) {
+            const uint32_t old = atom_add_acq_rel(&rel[u.slot], 1u);
+            if (old % NW == NW - 1 && nrel + S < nload && !abort_flag) issue(nrel + S);
+        }
+        ++nrel;
     };
 
     Segs seg{g0, g1, nz, 0, 0, 0};
@@ -324,15 +352,15 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         const int y0 = seg.t * zc.TY;
         float4 prev[IPT][2], cur[IPT][2];
         uint32_t off[IPT];       // element offset of the item in the current plane (cells < 2^32)
-        bool zero_u[IPT], zero_d[IPT];
+        bool edge_u[IPT], edge_d[IPT];   // rows at an absorbing y face (lateral tally)
 #pragma unroll
         for (int it = 0; it < IPT; ++it) {
             const int yg = y0 + ty_[it];
             off[it] = ((uint32_t)za * (uint32_t)ny + (uint32_t)yg) * (uint32_t)nx + 4u * (uint32_t)c4_[it];
-            zero_u[it] = !PERIODIC && yg == 0;
-            zero_d[it] = !PERIODIC && yg == ny - 1;
+            edge_u[it] = !PERIODIC && yg == 0;
+            edge_d[it] = !PERIODIC && yg == ny - 1;
         }
-        if (za > 0) {
+        {
             wait_full(pos);
             const float *sl = ring + (size_t)pos.slot * zc.slot;
 #pragma unroll
@@ -342,9 +370,6 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
             }
             release(pos);
             pos.advance(S);
-        } else {
-#pragma unroll
-            for (int it = 0; it < IPT; ++it) prev[it][0] = prev[it][1] = zero4;
         }
         wait_full(pos);
         RingPos pc = pos;
@@ -362,9 +387,8 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         // not unrolled: an unrolled march (which would save the register
         // rotation of prev/cur) measured slower
         for (int k = za; k < zb; ++k) {
-            const bool has_next = k + 1 < nz;
             const bool electrode = k == 0 || k == nz - 1;
-            if (has_next) wait_full(pos);
+            wait_full(pos);
             const float *sk = ring + (size_t)pc.slot * zc.slot;
             const float *sn = ring + (size_t)pos.slot * zc.slot;
             float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
@@ -377,27 +401,25 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                 for (int s = 0; s < 2; ++s) {
                     const float *bk = sk + s * sp_ofs;
                     const float4 n = cur[it][s];
-                    float4 u = *reinterpret_cast<const float4 *>(bk + o_u[it]);
-                    float4 d = *reinterpret_cast<const float4 *>(bk + o_d[it]);
-                    const float4 zp = has_next ? *reinterpret_cast<const float4 *>(sn + s * sp_ofs + o_c[it]) : zero4;
+                    const float4 u = *reinterpret_cast<const float4 *>(bk + o_u[it]);
+                    const float4 d = *reinterpret_cast<const float4 *>(bk + o_d[it]);
+                    const float4 zp = *reinterpret_cast<const float4 *>(sn + s * sp_ofs + o_c[it]);
                     float l = bk[o_l[it]];
                     float r = bk[o_r[it]];
                     if (!PERIODIC) {
-                        if (zero_u[it]) u = zero4;
-                        if (zero_d[it]) d = zero4;
                         if (c4_[it] == 0) l = 0.f;
                         if (c4_[it] == ncol4 - 1) r = 0.f;
                     }
                     const float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
                                             cf.wzm[s], cf.wzp[s], cf.adt);
-                    if (valid[it] && !failed) {
+                    if (valid[it]) {
                         *reinterpret_cast<float4 *>((s ? outm : outp) + off[it]) = v;
                         if (electrode) an[s] += (n.x + n.y) + (n.z + n.w);
                         if (!PERIODIC) {
                             if (c4_[it] == 0) lat[s] += n.x;
                             if (c4_[it] == ncol4 - 1) lat[s] += n.w;
-                            if (zero_u[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
-                            if (zero_d[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
+                            if (edge_u[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
+                            if (edge_d[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
                         }
                     }
                     prev[it][s] = n;
@@ -417,27 +439,23 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
             if (k == 0) { flush(1, an[0]); flush(2, an[1]); }
             if (k == nz - 1) { flush(3, an[0]); flush(4, an[1]); }
             release(pc);
-            if (has_next) { pc = pos; pos.advance(S); }
+            pc = pos;
+            pos.advance(S);
         }
         flush(0, rsum);
         if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); }
-        if (zb < nz) release(pc);   // the z1 halo plane of this segment
+        release(pc);   // the plane zb above the segment
         if (failed) break;
     }
-    if (failed && lane == 0) {
-        abort_flag = 1;
-        atomicExch(err, 1);
-    }
-    if (is_producer && (failed || abort_flag)) {
-        // every issued load must land before the CTA may exit: wait (bounded)
-        // for the last phase issued on each slot
-        for (int j = 0; j < S; ++j) {
-            if ((uint32_t)j >= pr.issued) break;
-            const uint32_t ph = j < pr.pos.slot ? pr.pos.phase : (pr.pos.phase ^ 1u);
-            (void)mbar_wait_bounded(&full[j], ph);
-        }
-    }
+    if (failed && lane == 0) atomicExch(err, 1);
     __syncthreads();
+    if (tid == 0) {
+        // no load may be in flight when the CTA exits: wait (bounded) for the
+        // last load issued into each slot (already complete unless a wait
+        // was lost)
+        for (int j = 0; j < S; ++j)
+            if (fills[j] > 0) (void)mbar_wait_bounded(&full[j], (fills[j] - 1u) & 1u);
+    }
     if (tid == 0 && !abort_flag) {
         double acc[7];
         for (int q = 0; q < 7; ++q) {
@@ -573,7 +591,7 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid
     z.S = want_s > 0 ? want_s : 8;
     if (z.S < 3 || z.S > 16) { set_error("z-march ring depth must be 3..16"); return IT_EINVAL; }
     for (;;) {
-        z.smem = (size_t)z.S * z.slot * sizeof(float) + 16 * z.S + 128;   // ring + barriers + alignment slack
+        z.smem = (size_t)z.S * z.slot * sizeof(float) + 16 * z.S + 128;   // ring + barriers/counters + alignment slack
         if (z.smem <= budget || z.S == 3 || want_s > 0) break;
         --z.S;
     }
