@@ -152,6 +152,41 @@ def cpu_oracle_rate(w, tracks, seconds):
     return w.cells * n / el / 1e9, int(os.environ.get("OMP_NUM_THREADS", cores)), n, el
 
 
+def continuous_roofline(B, synth, dev, steps=500):
+    """Step-kernel rate on the continuous-beam grid 512x512x256 (FP32, 1.07 GB
+    of state with the ping-pong set): the Poisson arrivals of the first three
+    steps at 3e9 tracks/(cm^2 s) deposited (a dense field), the launch shape
+    autotuned, then `steps` graph-replayed steps timed with CUDA events on the
+    library stream."""
+    import torch
+    w = synth.continuous_512x512x256()
+    npk = B.it_peak_density([200.0], [w.b_cm])
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        sim = B.Simulation(w.nx, w.ny, w.nz, w.dx_cm, w.voltage_V, n_peak_cm3=npk, torch_state=True)
+    try:
+        dt = sim.tallies().dt_s
+        tr = synth.poisson_tracks(w.seed, 1e7 * 300, w.nx * w.dx_cm, w.ny * w.dx_cm, dt, 3, w.b_cm,
+                                  synth.CONTINUOUS_LET)
+        sim.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        sim.autotune(trial_steps=8)
+        sim.step(64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        peak, kind = hbm_peak()
+        ach = BYTES_PER_CELL_UPDATE * w.cells / t / 1e9
+        return {"workload": w.name, "cells": w.cells, "kernel_us": t * 1e6,
+                "gcell_updates_per_s": w.cells / t / 1e9, "achieved_GBs": ach, "peak_GBs": peak,
+                "peak_kind": kind, "frac": ach / peak, "launch": sim.launch(), "tracks": len(tr)}
+    finally:
+        sim.close()
+
+
 def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=None):
     """Solves/s of the 256-simulation batch (uneven grids 32^3 .. 128x128x200,
     one launch per step for all running simulations, CUDA-graph segments)
@@ -368,6 +403,9 @@ def run_ours(args, ws, rank, local):
     achieved = BYTES_PER_CELL_UPDATE * cells / t_kernel / 1e9
     traffic = ncu_traffic()
 
+    cont = None
+    if rank == 0 and not args.no_continuous:
+        cont = continuous_roofline(B, synth, dev)
     batched = None
     if not args.no_batched:
         batched = batched_vs_plain(B, synth)
@@ -403,6 +441,7 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": args.steps * (seg + 4),   # per step: 4 deposit kernels + seg step kernels
             "clocks": clocks,
             "f_last": t.f,
+            "roofline_continuous_512x512x256": cont,
             "batched": batched,
             "surrogate": sur,
         }
@@ -426,6 +465,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain solves/s measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-vs-plain solves/s measurement")
+    ap.add_argument("--no-continuous", action="store_true", help="skip the 512x512x256 step-kernel roofline line")
     ap.add_argument("--launch", default="", help="fixed z-march shape TY,ctas_per_sm,stages,grid (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:

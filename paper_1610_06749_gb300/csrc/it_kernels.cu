@@ -120,29 +120,66 @@ int launch_step_simple_raw_f32(const float *ip, const float *im, float *op, floa
 // ---------------------------------------------------------------------------
 // monitor: in-domain ions and extreme densities of the current state
 // ---------------------------------------------------------------------------
+// Per-thread accumulation of one cell of each species: FP32 (or FP64)
+// partial sums over at most 32 cells, then FP64.
+template <typename T>
+struct MonAcc {
+    double sum[2] = {0.0, 0.0};
+    T part[2] = {0, 0};
+    int np = 0;
+    T mn[2] = {(T)INFINITY, (T)INFINITY}, mx[2] = {(T)-INFINITY, (T)-INFINITY};
+    __device__ __forceinline__ void add(T a, T b) {
+        part[0] += a; part[1] += b;          // a NaN propagates into the sums
+        mn[0] = a < mn[0] ? a : mn[0]; mn[1] = b < mn[1] ? b : mn[1];
+        mx[0] = a > mx[0] ? a : mx[0]; mx[1] = b > mx[1] ? b : mx[1];
+        if (++np == 32) {
+            sum[0] += (double)part[0]; sum[1] += (double)part[1];
+            part[0] = part[1] = 0; np = 0;
+        }
+    }
+};
+
+// In-domain sums and extremes of both species, one row of NM values per CTA.
+// FP32 states on 16-byte boundaries are read as float4 (four loads of each
+// species in flight per thread); other cells are read one by one.
 template <typename T>
 __global__ void __launch_bounds__(256)
 monitor_kernel(const T *__restrict__ ip, const T *__restrict__ im, size_t total, double vol,
                double *__restrict__ mon) {
     __shared__ double red[32 * 2];
     __shared__ double rmin[32 * 2], rmax[32 * 2];
-    double sum[2] = {0, 0};
-    T part[2] = {0, 0};
-    int np = 0;
-    T mnT[2] = {(T)INFINITY, (T)INFINITY}, mxT[2] = {(T)-INFINITY, (T)-INFINITY};
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const T a = ip[idx], b = im[idx];
-        part[0] += a; part[1] += b;          // a NaN propagates into the sums
-        mnT[0] = a < mnT[0] ? a : mnT[0]; mnT[1] = b < mnT[1] ? b : mnT[1];
-        mxT[0] = a > mxT[0] ? a : mxT[0]; mxT[1] = b > mxT[1] ? b : mxT[1];
-        if (++np == 32) {                    // partial sums in T over at most 32 cells, then FP64
-            sum[0] += (double)part[0]; sum[1] += (double)part[1];
-            part[0] = part[1] = 0; np = 0;
+    MonAcc<T> acc;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nthr = (size_t)gridDim.x * blockDim.x;
+    size_t done = 0;
+    const bool vec = sizeof(T) == 4 && (((uintptr_t)ip | (uintptr_t)im) & 15) == 0;
+    if (vec) {
+        const size_t n4 = total / 4;
+        const float4 *p4 = reinterpret_cast<const float4 *>(ip);
+        const float4 *m4 = reinterpret_cast<const float4 *>(im);
+        size_t q = tid;
+        for (; q + 3 * nthr < n4; q += 4 * nthr) {
+            float4 a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = __ldcs(p4 + q + u * nthr);
+                b[u] = __ldcs(m4 + q + u * nthr);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc.add(a[u].x, b[u].x); acc.add(a[u].y, b[u].y);
+                acc.add(a[u].z, b[u].z); acc.add(a[u].w, b[u].w);
+            }
         }
+        for (; q < n4; q += nthr) {
+            const float4 a = __ldcs(p4 + q), b = __ldcs(m4 + q);
+            acc.add(a.x, b.x); acc.add(a.y, b.y); acc.add(a.z, b.z); acc.add(a.w, b.w);
+        }
+        done = n4 * 4;
     }
-    sum[0] += (double)part[0]; sum[1] += (double)part[1];
-    double mn[2] = {(double)mnT[0], (double)mnT[1]}, mx[2] = {(double)mxT[0], (double)mxT[1]};
+    for (size_t idx = done + tid; idx < total; idx += nthr) acc.add(ip[idx], im[idx]);
+    double sum[2] = {acc.sum[0] + (double)acc.part[0], acc.sum[1] + (double)acc.part[1]};
+    double mn[2] = {(double)acc.mn[0], (double)acc.mn[1]}, mx[2] = {(double)acc.mx[0], (double)acc.mx[1]};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
 #pragma unroll
@@ -372,18 +409,44 @@ deposit_plane_kernel(const double *__restrict__ tr, const double *__restrict__ w
     if (tid == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = r[0];
 }
 
-// n += plane on every z plane: one thread per (i, j) column, coalesced per plane
-template <typename T>
-__global__ void deposit_apply_kernel(T *__restrict__ p, T *__restrict__ m, const double *__restrict__ plane,
-                                     size_t plane_n, int nz) {
-    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= plane_n) return;
-    const double a = plane[c];
-    if (a == 0.0) return;   // x + 0 == x: nothing to write
-    for (int k = 0; k < nz; ++k) {
-        const size_t idx = (size_t)k * plane_n + c;
-        p[idx] = (T)((double)p[idx] + a);
-        m[idx] = (T)((double)m[idx] + a);
+// n += plane on every z plane.  Thread = V adjacent columns (float4 when the
+// state is FP32 and nx % 4 == 0) over a chunk of DEP_KCHUNK planes
+// (blockIdx.y); columns the deposit did not reach are skipped.  Each cell is
+// rounded as T(double(n) + plane) in every variant.
+constexpr int DEP_KCHUNK = 8;
+template <typename T, int V>
+__global__ void __launch_bounds__(256)
+deposit_apply_kernel(T *__restrict__ p, T *__restrict__ m, const double *__restrict__ plane, size_t plane_n,
+                     int nz) {
+    const size_t c0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (c0 >= plane_n) return;
+    double a[V];
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        a[v] = plane[c0 + v];
+        any |= a[v] != 0.0;
+    }
+    if (!any) return;   // x + 0 == x: nothing to write
+    const int k0 = blockIdx.y * DEP_KCHUNK, k1 = min(nz, k0 + DEP_KCHUNK);
+    if constexpr (V == 4) {
+        float4 *p4 = reinterpret_cast<float4 *>(p), *m4 = reinterpret_cast<float4 *>(m);
+        for (int k = k0; k < k1; ++k) {
+            const size_t i4 = ((size_t)k * plane_n + c0) / 4;
+            float4 x = p4[i4], y = m4[i4];
+            x.x = (float)((double)x.x + a[0]); x.y = (float)((double)x.y + a[1]);
+            x.z = (float)((double)x.z + a[2]); x.w = (float)((double)x.w + a[3]);
+            y.x = (float)((double)y.x + a[0]); y.y = (float)((double)y.y + a[1]);
+            y.z = (float)((double)y.z + a[2]); y.w = (float)((double)y.w + a[3]);
+            p4[i4] = x;
+            m4[i4] = y;
+        }
+    } else {
+        for (int k = k0; k < k1; ++k) {
+            const size_t idx = (size_t)k * plane_n + c0;
+            p[idx] = (T)((double)p[idx] + a[0]);
+            m[idx] = (T)((double)m[idx] + a[0]);
+        }
     }
 }
 
@@ -416,13 +479,16 @@ int launch_deposit(it_ctx *c, int64_t n, cudaStream_t s) {
                                                             periodic ? 1 : 0, 1.0 / (c->dx * c->dx),
                                                             1.0 / c->p.W_eV, c->d_plane, part);
     IT_CK(cudaGetLastError());
-    const unsigned nb = (unsigned)((pn + 255) / 256);
-    if (c->prec == IT_FP32)
-        deposit_apply_kernel<float><<<nb, 256, 0, s>>>((float *)c->n[c->cur][0], (float *)c->n[c->cur][1],
-                                                       c->d_plane, (size_t)pn, c->g.nz);
+    const unsigned kchunks = (unsigned)((c->g.nz + DEP_KCHUNK - 1) / DEP_KCHUNK);
+    if (c->prec == IT_FP32 && nx % 4 == 0)
+        deposit_apply_kernel<float, 4><<<dim3((unsigned)((pn / 4 + 255) / 256), kchunks), 256, 0, s>>>(
+            (float *)c->n[c->cur][0], (float *)c->n[c->cur][1], c->d_plane, (size_t)pn, c->g.nz);
+    else if (c->prec == IT_FP32)
+        deposit_apply_kernel<float, 1><<<dim3((unsigned)((pn + 255) / 256), kchunks), 256, 0, s>>>(
+            (float *)c->n[c->cur][0], (float *)c->n[c->cur][1], c->d_plane, (size_t)pn, c->g.nz);
     else
-        deposit_apply_kernel<double><<<nb, 256, 0, s>>>((double *)c->n[c->cur][0], (double *)c->n[c->cur][1],
-                                                        c->d_plane, (size_t)pn, c->g.nz);
+        deposit_apply_kernel<double, 1><<<dim3((unsigned)((pn + 255) / 256), kchunks), 256, 0, s>>>(
+            (double *)c->n[c->cur][0], (double *)c->n[c->cur][1], c->d_plane, (size_t)pn, c->g.nz);
     IT_CK(cudaGetLastError());
     const double factor = c->dx * c->dx * (c->dx * c->g.nz);
     deposit_released_kernel<<<1, 256, 0, s>>>(part, nparts, factor, c->d_acc);
