@@ -193,7 +193,8 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
     against the plain one-context-per-simulation solver on the same GPU.
     The plain solver runs a subset (the first n_subset simulations); the batch
     is timed on that subset too, and on all 256.  Context creation is outside
-    the timed regions; deposition and the run to completion are inside.
+    the timed regions; deposition, the batch autotuner (it_batch_autotune)
+    and the run to completion are inside.
     Runs to completion use the upwind drift: at the recombination-bound time
     step the Courant number is small and Lax-Wendroff's undershoots make the
     explicit recombination term a source (it diverges, in the FP64 oracle
@@ -216,15 +217,18 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
             tr = tracks[q]
             bt.deposit(k, tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
         bt.retime()                      # dt bound from each deposited peak (overlaps included)
+        ta = time.perf_counter()
+        tune_us = bt.autotune(trial_steps=8)
+        ta = time.perf_counter() - ta
         launches = bt.run(tol=tol, check_every=check_every)
         el = time.perf_counter() - t0
         out = [bt.tallies(k) for k in range(len(idx))]
         bt.close()
-        return el, out, launches
+        return el, out, launches, (ta, tune_us)
 
-    t_all, tal_all, launches = run_batch(list(range(len(sims))))
+    t_all, tal_all, launches, tune = run_batch(list(range(len(sims))))
     sub = list(range(n_subset))
-    t_bsub, tal_bsub, _ = run_batch(sub)
+    t_bsub, tal_bsub, _, _ = run_batch(sub)
     ctxs = [B.Simulation(sims[q]["nx"], sims[q]["ny"], sims[q]["nz"], sims[q]["dx_cm"], sims[q]["voltage_V"],
                          n_peak_cm3=sims[q]["n_peak_cm3"], scheme=scheme) for q in sub]
     torch.cuda.synchronize()
@@ -242,6 +246,7 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
     df = max(abs(a.f - b) for a, b in zip(tal_bsub, f_plain))
     cell_updates = sum(sims[q]["nx"] * sims[q]["ny"] * sims[q]["nz"] * tal_all[q].steps for q in range(len(sims)))
     return {"sims": len(sims), "solves_per_s": len(sims) / t_all, "seconds": t_all, "step_launches": launches,
+            "autotune_s": tune[0], "autotuned_us_per_step": tune[1],
             "Gcell_updates_per_s": cell_updates / t_all / 1e9,
             "subset": n_subset, "subset_batched_solves_per_s": n_subset / t_bsub,
             "subset_plain_solves_per_s": n_subset / t_plain,

@@ -288,6 +288,18 @@ int it_batch_retime(it_batch *b);
 /* Cells per work-table entry (one CTA each; default 16384). */
 int it_batch_set_chunk(it_batch *b, int64_t cells_per_block);
 
+/* Native autotuner of the batched launch shape: after the deposits (and
+ * it_batch_retime), before the first step.  Times trial_steps (>= 2, rounded
+ * up to even) batched steps of the deposited state for each candidate --
+ * float4-kernel z splits aiming at 1..32 CTAs per SM, times 4096 / 16384 /
+ * 65536 cells per scalar-kernel entry -- with CUDA events on the batch
+ * stream, restores the deposited state after every trial (it allocates a
+ * temporary copy of one state set, freed before return), keeps the fastest
+ * and stores its microseconds per step in *best_us (may be NULL).  No tally
+ * changes.  IT_ESTATE after the first step.  The paper has no batching; the
+ * shape only changes the work split, not any cell's arithmetic. */
+int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us);
+
 /* Run every simulation until its in-domain charge / released < tol or it
  * has taken max_steps steps, checked every check_every steps (rounded up to
  * even).  *launches (may be NULL) receives the number of step launches. */

@@ -104,6 +104,7 @@ def lib():
                                     ctypes.POINTER(P)]),
             "it_batch_deposit_tracks": (I, [P, ctypes.c_int32, I64, DP, DP, DP]),
             "it_batch_set_chunk": (I, [P, I64]),
+            "it_batch_autotune": (I, [P, ctypes.c_int32, ctypes.POINTER(D)]),
             "it_batch_set_pulses": (I, [P, ctypes.c_int32, ctypes.c_int32, I64]),
             "it_batch_run": (I, [P, D, I64, I64, I64P]),
             "it_batch_tallies": (I, [P, ctypes.c_int32, ctypes.POINTER(it_tallies_t)]),
@@ -315,6 +316,12 @@ def it_batch_set_chunk(h, cells_per_block):
     _check(lib().it_batch_set_chunk(h, int(cells_per_block)))
 
 
+def it_batch_autotune(h, trial_steps=8) -> float:
+    us = ctypes.c_double()
+    _check(lib().it_batch_autotune(h, int(trial_steps), ctypes.byref(us)))
+    return us.value
+
+
 def it_batch_run(h, tol=1e-6, max_steps=10_000_000, check_every=64) -> int:
     n = ctypes.c_int64()
     _check(lib().it_batch_run(h, float(tol), int(max_steps), int(check_every), ctypes.byref(n)))
@@ -462,6 +469,9 @@ class Batch:
 
     def set_chunk(self, cells):
         it_batch_set_chunk(self.h, cells)
+
+    def autotune(self, trial_steps=8) -> float:
+        return it_batch_autotune(self.h, trial_steps)
 
     def run(self, tol=1e-6, max_steps=10_000_000, check_every=64):
         return it_batch_run(self.h, tol, max_steps, check_every)

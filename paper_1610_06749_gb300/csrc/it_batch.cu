@@ -310,6 +310,7 @@ struct it_batch {
     double *d_slots, *d_mon;
     size_t tab_cap, stab_cap, vtab_cap, slot_cap, act_cap;
     long long chunk;                  // cells per entry
+    int vec_cps;                      // CTAs per SM the float4 launch aims for (sets its z split)
     // per simulation
     std::vector<int64_t> steps;
     std::vector<char> active;
@@ -358,8 +359,9 @@ int build_table(it_batch *b) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long chunk = std::max(1024LL, std::min(b->chunk, active_cells / (4LL * sms)));
-    // z splits so that the float4 launch keeps about 4 CTAs per SM busy
-    const long long zsplit = vec_tiles > 0 ? std::max(1LL, (4LL * sms + vec_tiles - 1) / vec_tiles) : 1;
+    // z splits so that the float4 launch keeps about vec_cps CTAs per SM busy
+    const long long zsplit =
+        vec_tiles > 0 ? std::max(1LL, ((long long)b->vec_cps * sms + vec_tiles - 1) / vec_tiles) : 1;
     std::vector<int> vfirst, vcount, sfirst, scount, vsim, ssim;
     for (int s = 0; s < b->nsim; ++s) {
         if (!b->active[s]) continue;
@@ -553,6 +555,7 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
     b->pulse_done.assign(nsim, 0);
     b->pulse_period.assign(nsim, 0);
     b->chunk = 16384;
+    b->vec_cps = 4;
     b->graph_parity = -1;
     size_t off = 0;
     for (int s = 0; s < nsim; ++s) {
@@ -748,6 +751,67 @@ int it_batch_set_chunk(it_batch *b, int64_t cells_per_block) {
     if (!b || cells_per_block < 256) return bfail(IT_EINVAL, "chunk must be at least 256 cells");
     b->chunk = cells_per_block;
     b->tab_dirty = true;
+    return IT_OK;
+}
+
+int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us) {
+    if (!b) return bfail(IT_EINVAL, "batch is NULL");
+    if (trial_steps < 2) return bfail(IT_EINVAL, "trial_steps must be at least 2");
+    if (b->bstep != 0) return bfail(IT_ESTATE, "the launch shape is tuned before the first step");
+    const int K = trial_steps + (trial_steps & 1);   // even: the state returns to set 0
+    const size_t bytes = sizeof(float) * b->total;
+    void *backup = nullptr;
+    IT_CK(cudaMalloc(&backup, 2 * bytes));
+    char *bk = (char *)backup;
+    int rc = IT_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMemcpyAsync(bk, b->state[0][0], bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(bk + bytes, b->state[0][1], bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "batch autotune set-up");
+    const long long chunk0 = b->chunk;
+    const int cps0 = b->vec_cps;
+    long long best_chunk = chunk0;
+    int best_cps = cps0;
+    double best = 1e300;
+    for (int cps : {1, 2, 4, 8, 16, 32}) {
+        for (long long chunk : {4096LL, 16384LL, 65536LL}) {
+            if (rc) break;
+            b->vec_cps = cps;
+            b->chunk = chunk;
+            rc = build_table(b);
+            for (int q = 0; q < 2 && !rc; ++q) rc = launch_batched_step(b, q & 1);
+            if (!rc && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "event");
+            for (int q = 0; q < K && !rc; ++q) rc = launch_batched_step(b, q & 1);
+            if (!rc && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "event");
+            float ms = 0.f;
+            if (!rc) {
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) rc = cuda_fail(e, "batch autotune timing");
+            }
+            // the trial steps changed the state: put the deposited state back
+            if (cudaMemcpyAsync(b->state[0][0], bk, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+                cudaMemcpyAsync(b->state[0][1], bk + bytes, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+                rc = rc ? rc : cuda_fail(cudaGetLastError(), "batch autotune restore");
+            if (!rc && ms * 1e3 / K < best) {
+                best = ms * 1e3 / K;
+                best_chunk = chunk;
+                best_cps = cps;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->stream);
+    cudaFree(backup);
+    // the chosen shape; the next table build also clears the trial tallies
+    b->chunk = rc ? chunk0 : best_chunk;
+    b->vec_cps = rc ? cps0 : best_cps;
+    b->tab_dirty = true;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    if (rc) return rc;
+    if (best_us) *best_us = best;
     return IT_OK;
 }
 

@@ -233,7 +233,9 @@ def batch_tracks(desc) -> TrackList:
 # surrogate workload: configurations described by six inputs
 # ---------------------------------------------------------------------------
 
-SURROGATE_SECTION_CM = 0.025     # lateral section 0.25 mm x 0.25 mm (the paper's typical section)
+SURROGATE_DX_CM = 5e-4           # one grid spacing for every surrogate configuration
+SURROGATE_NX = 48                # lateral section 48 x 48 cells = 0.24 mm x 0.24 mm
+SURROGATE_SECTION_CM = SURROGATE_NX * SURROGATE_DX_CM
 SURROGATE_CHECK = 64             # pulse periods are whole multiples of this many steps
 
 
@@ -241,25 +243,26 @@ def surrogate_configs(seed: int, n: int):
     """n seeded configurations for the surrogate.
 
     Inputs (the six the network sees): LET (log-uniform 1-1000 keV/um),
-    voltage (50-400 V), gap (0.1-0.5 mm), b (5-20 um), tracks per pulse
-    (1-500 on the fixed 0.25 mm section) and pulse period (0 = a single
-    pulse with probability 1/2, else log-uniform 1-30 us for a train of 4
-    pulses).  The grid follows from them: dx = clamp(b/2, 4 um, 8 um), the
-    section and the gap in whole cells (nx a multiple of 4).  Draws per
-    configuration: 8 uniforms.
+    voltage (50-400 V), gap (20-100 cells of 5 um: 0.1-0.5 mm), b (5-20 um),
+    tracks per pulse (1-500 on the fixed 0.24 mm section) and pulse period
+    (0 = a single pulse with probability 1/2, else log-uniform 1-30 us for a
+    train of 4 pulses).  The grid is the same for every configuration (dx =
+    5 um, 48 x 48 cells) and the gap is a whole number of cells, so every
+    input is represented exactly and f is a continuous function of them: a
+    grid spacing that follows b would round the section and the gap to whole
+    cells differently for nearby inputs, and the simulated track density
+    would jump with it.  Draws per configuration: 8 uniforms.
     """
     u = uniform01(seed, 8 * n).reshape(n, 8)
     out = []
+    dx, nx = SURROGATE_DX_CM, SURROGATE_NX
     for k in range(n):
         let = 10.0 ** (3.0 * u[k, 0])
         V = 50.0 + 350.0 * u[k, 1]
-        gap = 0.01 + 0.04 * u[k, 2]
+        nz = 20 + int(u[k, 2] * 81)
         b = (5.0 + 15.0 * u[k, 3]) * 1e-4
         ntr = 1 + int(u[k, 4] * 500)
         period = 0.0 if u[k, 5] < 0.5 else 10.0 ** (-6.0 + 1.5 * u[k, 6])
-        dx = min(max(b / 2.0, 4e-4), 8e-4)
-        nx = max(8, int(round(SURROGATE_SECTION_CM / dx / 4.0)) * 4)
-        nz = max(8, int(round(gap / dx)))
         out.append(dict(let=let, voltage_V=V, b_cm=b, n_tracks=ntr, period_s=period,
                         pulses=1 if period == 0.0 else 4, nx=nx, ny=nx, nz=nz, dx_cm=dx,
                         gap_cm=nz * dx, seed=seed * 100003 + k))

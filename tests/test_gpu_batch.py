@@ -58,6 +58,35 @@ def test_batch_equals_single_contexts_bitwise(bc):
                 np.testing.assert_allclose(tb.released, ts.released, rtol=1e-15)
 
 
+def test_batch_autotune_keeps_the_state_and_changes_only_the_work_split():
+    cases = small_descs()
+    steps = 24
+    runs = []
+    for tune in (False, True):
+        with B.Batch([d for d, _ in cases]) as bt:
+            for q, (_, tr) in enumerate(cases):
+                bt.deposit(q, tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+            before = [bt.tallies(q) for q in range(len(cases))]
+            if tune:
+                us = bt.autotune(trial_steps=4)
+                assert np.isfinite(us) and us > 0
+                after = [bt.tallies(q) for q in range(len(cases))]
+                for t0, t1 in zip(before, after):   # trial steps leave no trace
+                    assert t1.steps == 0 and t1.recombined == 0.0
+                    np.testing.assert_array_equal(t1.in_domain, t0.in_domain)
+            bt.run(tol=0.0, max_steps=steps, check_every=8)
+            if tune:
+                with pytest.raises(B.ItError):
+                    bt.autotune()            # only before the first step
+            runs.append(([bt.density(q, 0) for q in range(len(cases))],
+                         [bt.tallies(q) for q in range(len(cases))]))
+    (d0, t0), (d1, t1) = runs
+    for q in range(len(cases)):
+        assert np.array_equal(d0[q], d1[q]), f"sim {q}"
+        assert t1[q].steps == t0[q].steps == steps
+        assert t1[q].f == pytest.approx(t0[q].f, abs=1e-12)
+
+
 def test_batch_runs_to_completion_and_matches_oracle():
     cases = small_descs()[:3]
     with B.Batch([d for d, _ in cases]) as bt:
