@@ -65,10 +65,13 @@ extern "C" {
  * blended derivative; IT_UPWIND the pure backward (upwind) difference. */
 #define IT_LAX_WENDROFF 0
 #define IT_UPWIND       1
-/* it_params.kernel: which step kernel runs (both are CUDA). */
+/* it_params.kernel: which step kernel runs (all are CUDA). */
 #define IT_KERNEL_AUTO   0   /* z-march kernel where the grid allows, else simple */
 #define IT_KERNEL_SIMPLE 1   /* one thread per cell, global loads */
 #define IT_KERNEL_ZMARCH 2   /* TMA-staged z-planes in shared memory (FP32, nx % 4 == 0) */
+#define IT_KERNEL_ZMARCH2 3  /* as IT_KERNEL_ZMARCH, two time steps per launch (temporal blocking
+                                of depth 2; nx/4 must divide 256 or 512 threads); densities are
+                                bitwise those of two single steps */
 
 typedef struct it_ctx it_ctx;
 
@@ -217,10 +220,13 @@ int it_reset(it_ctx *ctx);
  * it_step) and the context's stream (a cudaStream_t). */
 int it_device_state(it_ctx *ctx, void **plus, void **minus, void **stream);
 
-/* Choose the step kernel and, for IT_KERNEL_ZMARCH, its launch shape: rows
- * per tile (a divisor of ny), resident CTAs per SM and ring depth (3..16);
- * 0 leaves a value to the built-in rule.  Only before the first step
- * (IT_ESTATE otherwise).  IT_EINVAL if the shape does not fit the grid. */
+/* Choose the step kernel and, for IT_KERNEL_ZMARCH / IT_KERNEL_ZMARCH2, its
+ * launch shape: rows per tile (a divisor of ny; for IT_KERNEL_ZMARCH2 it is
+ * fixed at threads / (nx/4), 0 or that value), resident CTAs per SM (1: 16
+ * warps, 2: 8 warps each) and ring depth (3..16); 0 leaves a value to the
+ * built-in rule.  With IT_KERNEL_ZMARCH2, it_step runs steps in pairs and an
+ * odd last step on the simple kernel.  Only before the first step (IT_ESTATE
+ * otherwise).  IT_EINVAL if the shape does not fit the grid. */
 int it_set_launch(it_ctx *ctx, int kernel, int tile_rows, int ctas_per_sm, int stages);
 
 /* As it_set_launch, plus the grid of the z-march kernel: 0 = one CTA per
@@ -240,7 +246,8 @@ int it_set_launch_ex(it_ctx *ctx, int kernel, int tile_rows, int ctas_per_sm, in
  * step in microseconds. */
 int it_autotune(it_ctx *ctx, int trial_steps, int flags, double *best_us);
 
-/* Report the kernel in use, its launch shape and its CTA count. */
+/* Report the kernel in use, its launch shape and its CTA count (for
+ * IT_KERNEL_ZMARCH2, the CTAs of its two-step launches). */
 int it_get_launch(it_ctx *ctx, int *kernel, int *tile_rows, int *ctas_per_sm, int *stages, int *ctas);
 
 /* ---------------------------------------------------------------------------

@@ -21,7 +21,7 @@ IT_OK, IT_EINVAL, IT_ENOMEM, IT_ECUDA, IT_EUNSTABLE, IT_ETIMEOUT, IT_ESTATE = 0,
 IT_FP32, IT_FP64 = 0, 1
 IT_PERIODIC, IT_ABSORBING = 0, 1
 IT_LAX_WENDROFF, IT_UPWIND = 0, 1
-IT_KERNEL_AUTO, IT_KERNEL_SIMPLE, IT_KERNEL_ZMARCH = 0, 1, 2
+IT_KERNEL_AUTO, IT_KERNEL_SIMPLE, IT_KERNEL_ZMARCH, IT_KERNEL_ZMARCH2 = 0, 1, 2, 3
 
 _ERRNAMES = {IT_EINVAL: "IT_EINVAL", IT_ENOMEM: "IT_ENOMEM", IT_ECUDA: "IT_ECUDA",
              IT_EUNSTABLE: "IT_EUNSTABLE", IT_ETIMEOUT: "IT_ETIMEOUT", IT_ESTATE: "IT_ESTATE"}

@@ -65,7 +65,7 @@ static int check_params(const it_params *p, it_grid g, double dx) {
     if (p->precision != IT_FP32 && p->precision != IT_FP64) return fail(IT_EINVAL, "bad precision");
     if (p->lateral_bc != IT_PERIODIC && p->lateral_bc != IT_ABSORBING) return fail(IT_EINVAL, "bad lateral_bc");
     if (p->scheme != IT_LAX_WENDROFF && p->scheme != IT_UPWIND) return fail(IT_EINVAL, "bad scheme");
-    if (p->kernel < IT_KERNEL_AUTO || p->kernel > IT_KERNEL_ZMARCH) return fail(IT_EINVAL, "bad kernel");
+    if (p->kernel < IT_KERNEL_AUTO || p->kernel > IT_KERNEL_ZMARCH2) return fail(IT_EINVAL, "bad kernel");
     if (!(std::isfinite(p->cfl_safety) && p->cfl_safety > 0 && p->cfl_safety <= 1.0))
         return fail(IT_EINVAL, "cfl_safety must be in (0, 1]");
     if (!(std::isfinite(p->react_kappa) && p->react_kappa > 0)) return fail(IT_EINVAL, "react_kappa must be > 0");
@@ -204,7 +204,15 @@ static int validate_tracks(int64_t n, const double *xy, const double *let, const
 }
 
 static int one_step(it_ctx *c) {
+    // the two-step kernel's odd steps run on the simple kernel (bitwise the same cells)
     return c->kernel == IT_KERNEL_ZMARCH ? launch_step_zmarch(c, c->stream) : launch_step_simple(c, c->stream);
+}
+
+// two steps: one launch of the two-step kernel, else two single steps
+static int two_steps(it_ctx *c) {
+    if (c->kernel == IT_KERNEL_ZMARCH2) return launch_step_zmarch2(c, c->stream);
+    int rc = one_step(c);
+    return rc ? rc : one_step(c);
 }
 
 constexpr int kGraphSteps = 32;   // even: a segment returns to the same ping-pong set
@@ -218,7 +226,7 @@ static int run_plain(it_ctx *c, int64_t n) {
             cudaGraph_t g = nullptr;
             IT_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             int rc = IT_OK;
-            for (int q = 0; q < kGraphSteps && rc == IT_OK; ++q) rc = one_step(c);
+            for (int q = 0; q < kGraphSteps && rc == IT_OK; q += 2) rc = two_steps(c);
             cudaError_t e = cudaStreamEndCapture(c->stream, &g);
             c->cur = start;   // capture recorded the launches; nothing ran yet
             if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -232,7 +240,12 @@ static int run_plain(it_ctx *c, int64_t n) {
         n -= kGraphSteps;
         c->steps += kGraphSteps;
     }
-    for (int64_t q = 0; q < n; ++q) {
+    for (; n >= 2; n -= 2) {
+        int rc = two_steps(c);
+        if (rc) return rc;
+        c->steps += 2;
+    }
+    if (n == 1) {
         int rc = one_step(c);
         if (rc) return rc;
         c->steps += 1;
@@ -256,6 +269,10 @@ void coef_f32(const it_params *p, double dx, double dt, Coef<float> *out) { make
 int set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages, int grid) {
     if (kernel == IT_KERNEL_SIMPLE) {
         c->kernel = IT_KERNEL_SIMPLE;
+    } else if (kernel == IT_KERNEL_ZMARCH2) {
+        int rc = zmarch2_setup(c, tile_rows, ctas_per_sm, stages, grid);
+        if (rc) return rc;
+        c->kernel = IT_KERNEL_ZMARCH2;
     } else if (kernel == IT_KERNEL_ZMARCH || kernel == IT_KERNEL_AUTO) {
         int rc = zmarch_setup(c, tile_rows, ctas_per_sm, stages, grid);
         if (rc) {
@@ -267,7 +284,10 @@ int set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages
     } else {
         return fail(IT_EINVAL, "bad kernel");
     }
-    const int n = c->kernel == IT_KERNEL_ZMARCH ? c->zm_grid : simple_grid(c);
+    // the two-step kernel leaves odd steps to the simple kernel: slots for both
+    const int n = c->kernel == IT_KERNEL_ZMARCH    ? c->zm_grid
+                  : c->kernel == IT_KERNEL_ZMARCH2 ? std::max(c->zm2.grid, simple_grid(c))
+                                                   : simple_grid(c);
     if (n != c->nslots) {
         double *ns = nullptr;
         IT_CK(cudaMalloc(&ns, sizeof(double) * NT * n));
@@ -411,11 +431,18 @@ int it_create_ex(it_grid g, double dx_cm, double dt_s, const it_params *p, void 
         } else if (p->kernel == IT_KERNEL_ZMARCH) {
             return bail(rc);
         }
+    } else if (p->kernel == IT_KERNEL_ZMARCH2) {
+        rc = zmarch2_setup(c, 0, 0, 0, 0);
+        if (rc) return bail(rc);
+        c->kernel = IT_KERNEL_ZMARCH2;
     }
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    c->nslots = c->kernel == IT_KERNEL_ZMARCH ? c->zm_grid : simple_grid(c);
+    // the two-step kernel leaves odd steps to the simple kernel: slots for both
+    c->nslots = c->kernel == IT_KERNEL_ZMARCH    ? c->zm_grid
+                : c->kernel == IT_KERNEL_ZMARCH2 ? std::max(c->zm2.grid, simple_grid(c))
+                                                 : simple_grid(c);
     c->nmon = 2 * sms;
 
     if ((e = cudaMalloc(&c->d_slots, sizeof(double) * NT * c->nslots)) != cudaSuccess ||
@@ -659,12 +686,12 @@ int it_set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int sta
 
 int it_get_launch(it_ctx *c, int *kernel, int *tile_rows, int *ctas_per_sm, int *stages, int *ctas) {
     if (!c) return fail(IT_EINVAL, "ctx is NULL");
-    const bool zm = c->kernel == IT_KERNEL_ZMARCH;
+    const bool zm = c->kernel == IT_KERNEL_ZMARCH, zm2 = c->kernel == IT_KERNEL_ZMARCH2;
     if (kernel) *kernel = c->kernel;
-    if (tile_rows) *tile_rows = zm ? c->zm.TY : 0;
-    if (ctas_per_sm) *ctas_per_sm = zm ? c->zm.ctas_per_sm : 0;
-    if (stages) *stages = zm ? c->zm.S : 0;
-    if (ctas) *ctas = c->nslots;
+    if (tile_rows) *tile_rows = zm ? c->zm.TY : zm2 ? c->zm2.TY : 0;
+    if (ctas_per_sm) *ctas_per_sm = zm ? c->zm.ctas_per_sm : zm2 ? c->zm2.ctas_per_sm : 0;
+    if (stages) *stages = zm ? c->zm.S : zm2 ? c->zm2.S : 0;
+    if (ctas) *ctas = zm2 ? c->zm2.grid : c->nslots;
     return IT_OK;
 }
 

@@ -66,6 +66,20 @@ struct ZmConf {
     int ctas_per_sm;
 };
 
+// Launch shape of the two-steps-per-launch z-march kernel: tiles of TY
+// full-width rows, one float4 item per thread of the tile (TY * nx/4 ==
+// threads); a ring slot holds TY + 4 rows of both species (two halo rows
+// above and below), the intermediate level lives in two shared-memory planes
+// of TY + 2 rows.
+struct Zm2Conf {
+    int TY, ntile, S, bx, nbx;
+    int reg_top, reg_main, reg_bot;   // float offsets of the 2-row halos and TY rows in a ring block
+    int blk, slot;                    // floats per (species, x-box) ring block / per ring slot
+    int mblk, mslot;                  // floats per (species, x-box) intermediate block / per intermediate plane
+    size_t smem;
+    int threads, ctas_per_sm, grid;
+};
+
 // tallies of one context kept on the device
 struct DevAcc {
     double released[2];
@@ -86,7 +100,7 @@ struct it_ctx {
     void *state_base;
     cudaStream_t stream;
     bool own_stream;
-    int kernel;           // resolved IT_KERNEL_SIMPLE / IT_KERNEL_ZMARCH
+    int kernel;           // resolved IT_KERNEL_SIMPLE / IT_KERNEL_ZMARCH / IT_KERNEL_ZMARCH2
     int nslots;           // CTAs that own tally slots
     double *d_slots;      // [nslots][NT]
     double *d_mon;        // [nmon][NM]
@@ -116,6 +130,9 @@ struct it_ctx {
     int zm_grid;
     CUtensorMap tm_main[2][2];   // [set][species], box {bx, TY, 1}
     CUtensorMap tm_halo[2][2];   // [set][species], box {bx, 1, 1}
+    itk::Zm2Conf zm2;            // two steps per launch (IT_KERNEL_ZMARCH2)
+    CUtensorMap tm_main2[2][2];  // [set][species], box {bx, TY, 1}
+    CUtensorMap tm_halo2[2][2];  // [set][species], box {bx, 2, 1}
     itk::Coef<float> cf;
     itk::Coef<double> cd;
     int *d_err;           // device error flag (bounded waits that ran out)
@@ -138,6 +155,11 @@ int launch_step_simple(it_ctx *c, cudaStream_t s);
 int launch_step_zmarch(it_ctx *c, cudaStream_t s);
 int zmarch_configure(it_ctx *c);
 int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid);
+// FP32 3-D tensor map over [nz][ny][nx] with a box of bx x rows x 1 (it_zmarch.cu)
+int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx, int rows);
+// two steps per launch (it_zmarch2.cu)
+int zmarch2_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid);
+int launch_step_zmarch2(it_ctx *c, cudaStream_t s);
 int set_launch(it_ctx *c, int kernel, int tile_rows, int ctas_per_sm, int stages, int grid);
 int launch_finalize(it_ctx *c, cudaStream_t s);
 int launch_monitor(it_ctx *c, cudaStream_t s);

@@ -1,11 +1,12 @@
 // it_tune.cu -- native autotuner of the step kernel's launch shape.
 //
-// Candidates: the simple kernel, and the z-march kernel over tile heights
-// that give each thread one or two float4 items, 1 or 2 CTAs per SM, ring
-// depths 3..8 and the two grid rules (one CTA per resident slot, or a
-// multiple of the tile count).  Each candidate is timed with CUDA events on
-// the context stream over a few steps of the live state, which is saved
-// before and restored after every trial.
+// Candidates: the simple kernel; the z-march kernel over tile heights that
+// give each thread one or two float4 items, 1 or 2 CTAs per SM, ring depths
+// 3..8 and the two grid rules (one CTA per resident slot, or a multiple of
+// the tile count); and the two-steps-per-launch z-march kernel over 1 or 2
+// CTAs per SM, ring depths 3..6 and the two grid rules.  Each candidate is
+// timed with CUDA events on the context stream over a few steps of the live
+// state, which is saved before and restored after every trial.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -42,6 +43,16 @@ std::vector<Shape> candidates(const it_ctx *c) {
                 for (int grid : {0, -1}) v.push_back({IT_KERNEL_ZMARCH, ty, cps, s, grid});
         }
     }
+    // two steps per launch: one float4 per thread, so the tile height is
+    // threads / (nx/4)
+    for (int cps = 1; cps <= 2; ++cps) {
+        const int threads = cps == 1 ? 512 : 256;
+        if (threads % ncol4 != 0 || 2 * ncol4 > threads) continue;
+        const int ty = threads / ncol4;
+        if (ny % ty != 0 || ny < 4) continue;
+        for (int s : {3, 4, 5, 6})
+            for (int grid : {0, -1}) v.push_back({IT_KERNEL_ZMARCH2, ty, cps, s, grid});
+    }
     return v;
 }
 
@@ -53,11 +64,16 @@ int time_shape(it_ctx *c, const Shape &sh, int trial, const void *backup, size_t
     IT_CK(cudaEventCreate(&e0));
     IT_CK(cudaEventCreate(&e1));
     const int cur = c->cur;
-    for (int q = 0; q < 2 && rc == IT_OK; ++q) rc = c->kernel == IT_KERNEL_ZMARCH ? launch_step_zmarch(c, c->stream)
-                                                                               : launch_step_simple(c, c->stream);
+    // one launch: one step, or two with the two-step kernel (trial is even)
+    auto launch = [&]() {
+        return c->kernel == IT_KERNEL_ZMARCH    ? launch_step_zmarch(c, c->stream)
+               : c->kernel == IT_KERNEL_ZMARCH2 ? launch_step_zmarch2(c, c->stream)
+                                                : launch_step_simple(c, c->stream);
+    };
+    const int per = c->kernel == IT_KERNEL_ZMARCH2 ? 2 : 1;
+    for (int q = 0; q < 2 && rc == IT_OK; q += per) rc = launch();
     cudaEventRecord(e0, c->stream);
-    for (int q = 0; q < trial && rc == IT_OK; ++q) rc = c->kernel == IT_KERNEL_ZMARCH ? launch_step_zmarch(c, c->stream)
-                                                                                   : launch_step_simple(c, c->stream);
+    for (int q = 0; q < trial && rc == IT_OK; q += per) rc = launch();
     cudaEventRecord(e1, c->stream);
     cudaError_t e = cudaEventSynchronize(e1);
     float ms = 0.f;

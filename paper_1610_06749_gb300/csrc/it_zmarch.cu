@@ -32,59 +32,9 @@
 
 #include "it_device.cuh"
 #include "it_internal.cuh"
+#include "it_tma.cuh"
 
 namespace itk {
-
-// ---------------------------------------------------------------------------
-// PTX helpers: mbarrier + TMA
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// about 2^32 SM cycles (~2 s at 2 GHz) before a wait is declared lost
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 32)) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 struct ZmMaps {
     CUtensorMap main[2];   // n+, n- of the input set
@@ -92,107 +42,6 @@ struct ZmMaps {
 };
 
 constexpr int ZM_MAX_IPT = 4;                    // float4 items per thread
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Position in the ring: slot index and the parity of its current phase.
-struct RingPos {
-    int slot;
-    uint32_t phase;
-    __device__ __forceinline__ void advance(int S) {
-        if (++slot == S) { slot = 0; phase ^= 1u; }
-    }
-};
-
-// The CTA's work: tile-planes (y-tile t, plane z) in the order t*nz + z,
-// split into gridDim.x equal contiguous ranges.  A range is walked as
-// segments (one tile column each); a segment computing planes [za, zb) loads
-// planes za-1 .. zb.  The electrode ghost planes z = -1 and z = nz lie
-// outside the tensor, and TMA fills them with zeros (n = 0 at the electrodes).
-struct Segs {
-    long long L, g1;
-    int nz;
-    int t, za, zb;
-    __device__ __forceinline__ bool next() {
-        if (L >= g1) return false;
-        t = (int)(L / nz);
-        za = (int)(L - (long long)t * nz);
-        zb = (int)min((long long)nz, za + (g1 - L));
-        L += zb - za;
-        return true;
-    }
-    __device__ __forceinline__ int lo() const { return za - 1; }
-    __device__ __forceinline__ int hi() const { return zb; }
-};
-
-// Plane n of a CTA's load sequence: its segments in order, each loading
-// planes za-1 .. zb of its tile.  Returns false past the end.
-__device__ __forceinline__ bool plane_of(long long g0, long long g1, int nz, int n, int &t, int &z) {
-    long long L = g0;
-    while (L < g1) {
-        const int tt = (int)(L / nz);
-        const int za = (int)(L - (long long)tt * nz);
-        const int zb = (int)min((long long)nz, za + (g1 - L));
-        const int cnt = zb - za + 2;
-        if (n < cnt) {
-            t = tt;
-            z = za - 1 + n;
-            return true;
-        }
-        n -= cnt;
-        L += zb - za;
-    }
-    return false;
-}
-
-__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
-    uint32_t old;
-    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;"
-                 : "=r"(old)
-                 : "r"(smem_u32(p)), "r"(v)
-                 : "memory");
-    return old;
-}
-
-// Four cells of upd7 (one float4 x-segment) with paired FP32 operations:
-// each lane of a paired operation rounds exactly like the scalar operation,
-// and the sequence is the one of upd7, so the results are bitwise those of
-// the scalar kernels.
-__device__ __forceinline__ float4 upd7x4(float4 n, float l, float r, float4 u, float4 d, float4 zm, float4 zp,
-                                         float2 rxy, float2 rzw, float w0, float wx, float wy, float wzm, float wzp,
-                                         float adt) {
-    const float2 W0 = make_float2(w0, w0), WX = make_float2(wx, wx), WY = make_float2(wy, wy);
-    const float2 WZM = make_float2(wzm, wzm), WZP = make_float2(wzp, wzp), NA = make_float2(-adt, -adt);
-    float2 a = __fmul2_rn(W0, make_float2(n.x, n.y));
-    float2 b = __fmul2_rn(W0, make_float2(n.z, n.w));
-    a = __ffma2_rn(WX, make_float2(l + n.y, n.x + n.z), a);
-    b = __ffma2_rn(WX, make_float2(n.y + n.w, n.z + r), b);
-    a = __ffma2_rn(WY, __fadd2_rn(make_float2(u.x, u.y), make_float2(d.x, d.y)), a);
-    b = __ffma2_rn(WY, __fadd2_rn(make_float2(u.z, u.w), make_float2(d.z, d.w)), b);
-    a = __ffma2_rn(WZM, make_float2(zm.x, zm.y), a);
-    b = __ffma2_rn(WZM, make_float2(zm.z, zm.w), b);
-    a = __ffma2_rn(WZP, make_float2(zp.x, zp.y), a);
-    b = __ffma2_rn(WZP, make_float2(zp.z, zp.w), b);
-    a = __ffma2_rn(NA, rxy, a);
-    b = __ffma2_rn(NA, rzw, b);
-    return make_float4(a.x, a.y, b.x, b.y);
-}
 
 // Persistent step kernel: NW warps, all of them compute.
 //   The planes a CTA needs stream through an S-deep ring of shared-memory
@@ -495,7 +344,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx, int rows) {
+int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx, int rows) {
     auto fn = encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available");
