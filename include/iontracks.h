@@ -191,6 +191,23 @@ int it_step(it_ctx *ctx, int64_t n_steps);
 int it_run_to_completion(it_ctx *ctx, double tol, int64_t max_steps,
                          int64_t check_every, int64_t *steps_done);
 
+/* Continuous beam (Poisson arrivals scheduled with it_schedule_tracks; Sec.
+ * Implementation): step in windows of window_steps until the
+ * steady-state collection efficiency of two successive windows differs by
+ * less than tol, or until the next whole window would pass max_steps more
+ * steps.  The efficiency of a window counts the ions that left the domain
+ * during it, f_ss = dCol / (dCol + 2 dRec + dLost), over both species: dCol
+ * collected at either electrode, dRec recombined pairs (two ions each), dLost
+ * lost through absorbing lateral faces.  The cumulative f of it_tallies
+ * carries the ions still in flight; f_ss does not.  *f_ss (may be NULL)
+ * receives the last window's value (NaN when no ion left the domain in it),
+ * *stop (may be NULL) 0 when the steady state ended the run and 1 when the
+ * step limit did, *steps_done (may be NULL) the steps taken.  Returns
+ * IT_EUNSTABLE if the state went non-finite; reaching the step limit is not
+ * an error. */
+int it_run_to_steady_state(it_ctx *ctx, int64_t window_steps, double tol, int64_t max_steps, double *f_ss,
+                           int *stop, int64_t *steps_done);
+
 /* Synchronise and return all tallies (FP64, reduced in a fixed order so that
  * reruns are bitwise identical). */
 int it_tallies(it_ctx *ctx, it_tallies_t *out);

@@ -153,6 +153,34 @@ class Oracle:
                 ptr = hi
             self.step(1)
 
+    def run_to_steady_state(self, x_cm, y_cm, let, b, step_idx, window: int, tol: float, max_steps: int):
+        """Continuous beam to steady state (Sec. Implementation):
+        windows of `window` steps with the scheduled arrivals, until the
+        efficiency of the ions that left the domain in a window,
+        f_ss = dCol / (dCol + 2 dRec + dLost), changes by less than tol
+        between two windows, or until the next window would pass max_steps.
+        Returns (f_ss of the last window, stop: 0 steady / 1 step limit,
+        steps taken)."""
+        def gone(t):
+            return float(t.collected.sum()), float(t.recombined), float(t.lost_lateral.sum())
+        start = self.tallies().steps
+        c0, r0, l0 = gone(self.tallies())
+        f_prev = f_cur = float("nan")
+        n = 0
+        while self.tallies().steps - start + window <= max_steps:
+            s0 = self.tallies().steps
+            self.run_schedule(x_cm, y_cm, let, b, step_idx, window, start_step=s0)
+            c1, r1, l1 = gone(self.tallies())
+            dc, dr, dl = c1 - c0, r1 - r0, l1 - l0
+            c0, r0, l0 = c1, r1, l1
+            den = dc + 2.0 * dr + dl
+            f_cur = dc / den if den != 0.0 else float("nan")
+            n += 1
+            if n >= 2 and np.isfinite(f_cur) and np.isfinite(f_prev) and abs(f_cur - f_prev) < tol:
+                return f_cur, 0, self.tallies().steps - start
+            f_prev = f_cur
+        return f_cur, 1, self.tallies().steps - start
+
     def tallies(self) -> Tallies:
         lib = _load()
         t = np.zeros(10)

@@ -88,6 +88,7 @@ def lib():
             "it_schedule_tracks": (I, [P, I64, DP, DP, DP, I64P]),
             "it_step": (I, [P, I64]),
             "it_run_to_completion": (I, [P, D, I64, I64, I64P]),
+            "it_run_to_steady_state": (I, [P, I64, D, I64, DP, ctypes.POINTER(I), I64P]),
             "it_tallies": (I, [P, ctypes.POINTER(it_tallies_t)]),
             "it_get_density": (I, [P, I, P, SZ]),
             "it_set_density": (I, [P, P, P, SZ]),
@@ -225,6 +226,16 @@ def it_run_to_completion(h, tol=1e-6, max_steps=10_000_000, check_every=64) -> i
     done = ctypes.c_int64()
     _check(lib().it_run_to_completion(h, float(tol), int(max_steps), int(check_every), ctypes.byref(done)))
     return done.value
+
+
+def it_run_to_steady_state(h, window_steps=1000, tol=1e-5, max_steps=10_000_000):
+    """Returns (f_ss of the last window, stop: 0 steady / 1 step limit, steps taken)."""
+    f = ctypes.c_double()
+    stop = ctypes.c_int()
+    done = ctypes.c_int64()
+    _check(lib().it_run_to_steady_state(h, int(window_steps), float(tol), int(max_steps), ctypes.byref(f),
+                                        ctypes.byref(stop), ctypes.byref(done)))
+    return f.value, stop.value, done.value
 
 
 def it_tallies(h) -> it_tallies_t:
@@ -547,6 +558,9 @@ class Simulation:
 
     def run_to_completion(self, tol=1e-6, max_steps=10_000_000, check_every=64):
         return it_run_to_completion(self.h, tol, max_steps, check_every)
+
+    def run_to_steady_state(self, window_steps=1000, tol=1e-5, max_steps=10_000_000):
+        return it_run_to_steady_state(self.h, window_steps, tol, max_steps)
 
     def tallies(self) -> Tallies:
         return Tallies.from_c(it_tallies(self.h))

@@ -601,6 +601,45 @@ int it_run_to_completion(it_ctx *c, double tol, int64_t max_steps, int64_t check
     return rc;
 }
 
+int it_run_to_steady_state(it_ctx *c, int64_t window_steps, double tol, int64_t max_steps, double *f_ss, int *stop,
+                           int64_t *steps_done) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (window_steps < 1 || !(tol >= 0) || max_steps < 0) return fail(IT_EINVAL, "bad argument");
+    const int64_t start = c->steps;
+    it_tallies_t t;
+    int rc = it_tallies(c, &t);
+    // ions that have left the domain so far, by route
+    auto col = [](const it_tallies_t &x) {
+        return x.collected_anode[0] + x.collected_anode[1] + x.collected_cathode[0] + x.collected_cathode[1];
+    };
+    auto lost = [](const it_tallies_t &x) { return x.lost_lateral[0] + x.lost_lateral[1]; };
+    double c0 = col(t), r0 = t.recombined, l0 = lost(t);
+    double f_prev = std::nan(""), f_cur = std::nan("");
+    int code = 1;
+    int64_t windows = 0;
+    while (rc == IT_OK && c->steps - start + window_steps <= max_steps) {
+        rc = it_step(c, window_steps);
+        if (rc) break;
+        rc = it_tallies(c, &t);
+        if (rc) break;
+        if (!std::isfinite(t.in_domain[0] + t.in_domain[1] + t.recombined)) { rc = fail(IT_EUNSTABLE, "state is not finite"); break; }
+        const double dc = col(t) - c0, dr = t.recombined - r0, dl = lost(t) - l0;
+        c0 = col(t); r0 = t.recombined; l0 = lost(t);
+        const double gone = dc + 2.0 * dr + dl;   // a recombined pair removes two ions
+        f_cur = gone != 0.0 ? dc / gone : std::nan("");
+        ++windows;
+        if (windows >= 2 && std::isfinite(f_cur) && std::isfinite(f_prev) && std::fabs(f_cur - f_prev) < tol) {
+            code = 0;
+            break;
+        }
+        f_prev = f_cur;
+    }
+    if (f_ss) *f_ss = f_cur;
+    if (stop) *stop = code;
+    if (steps_done) *steps_done = c->steps - start;
+    return rc;
+}
+
 int it_get_density(it_ctx *c, int species, void *dst, size_t bytes) {
     if (!c || !dst || (species != 0 && species != 1)) return fail(IT_EINVAL, "bad argument");
     if (bytes != c->g.cells() * c->esize) return fail(IT_EINVAL, "bytes must equal cells * element size");

@@ -357,3 +357,42 @@ def test_contexts_with_different_tiles_coexist():
     finally:
         big.close()
         small.close()
+
+
+def test_steady_state_runner_matches_oracle():
+    # continuous beam on a small grid: Poisson arrivals, windows of 50 steps,
+    # the same stopping rule on both sides (FP32 GPU vs FP64 oracle)
+    nx, ny, nz, dx, V = 32, 32, 24, 5e-4, 200.0
+    npk = o.peak_track_density([200.0], [1e-3])
+    dt = o.dt_rule(dx, V, nz * dx, n_peak=npk, scheme=o.SCHEME_UPWIND)
+    tr = synth.poisson_tracks(77, 3e10, nx * dx, ny * dx, dt, 1500, 1e-3, synth.CONTINUOUS_LET)
+    assert len(tr) > 50
+    g, O = make_pair(nx, ny, nz, dx, V, tr, scheme=B.IT_UPWIND, dt=dt)
+    with g:
+        g.schedule(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step)
+        fg, sg, ng = g.run_to_steady_state(window_steps=50, tol=2e-3, max_steps=1500)
+        fo, so, no = O.run_to_steady_state(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step, 50, 2e-3, 1500)
+        assert (sg, ng) == (so, no)
+        assert fg == pytest.approx(fo, abs=1e-5)
+        compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
+
+
+def test_steady_state_of_a_sparse_track_train_is_the_single_track_f_on_gpu():
+    # identical tracks farther apart than a track's life: the steady-state
+    # window efficiency equals the single-track f (see the oracle pin)
+    nx, ny, nz, dx, V = 16, 16, 20, 5e-4, 300.0
+    let, b, P, n = 300.0, 1e-3, 400, 5
+    dt = o.dt_rule(dx, V, nz * dx, n_peak=o.peak_track_density([let], [b]), scheme=o.SCHEME_UPWIND)
+    kw = dict(dt_s=dt, lateral_bc=B.IT_ABSORBING, scheme=B.IT_UPWIND)
+    with B.Simulation(nx, ny, nz, dx, V, **kw) as one, B.Simulation(nx, ny, nz, dx, V, **kw) as train:
+        one.deposit([0.5 * nx * dx], [0.5 * ny * dx], [let], [b])
+        one.step(P)
+        f1 = one.tallies().f
+        steps = np.arange(n, dtype=np.int64) * P
+        train.schedule(np.full(n, 0.5 * nx * dx), np.full(n, 0.5 * ny * dx), np.full(n, let), np.full(n, b), steps)
+        f_ss, stop, done = train.run_to_steady_state(window_steps=P, tol=1e-7, max_steps=n * P)
+        assert stop == 0 and done == 2 * P
+        # the window sums are differences of cumulative FP64 tallies built
+        # from FP32 partials (1e-8 level); a miscounted route of the ions that
+        # left would be off by O(0.1)
+        assert f_ss == pytest.approx(f1, abs=1e-6)

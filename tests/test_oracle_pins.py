@@ -466,3 +466,41 @@ def test_upwind_stays_positive_where_lax_wendroff_undershoots():
         mins[sch] = lo
     assert mins[o.SCHEME_UPWIND] >= 0.0
     assert mins[o.SCHEME_LAX_WENDROFF] < 0.0
+
+
+# --------------------------------------------------------------------------
+# continuous beam: steady-state efficiency of the ions that left the domain
+# --------------------------------------------------------------------------
+def test_steady_state_of_a_sparse_track_train_is_the_single_track_f():
+    # Tracks of one LET at one position, P steps apart, with P longer than a
+    # track's life: no two tracks share the domain, so over any window of P
+    # steps the ions that leave are exactly one track's ions, and the window
+    # efficiency dCol / (dCol + 2 dRec + dLost) must equal the single-track f
+    # (collected / released at completion).  Counting the released ions of the
+    # window instead, or a recombined pair as one ion, breaks the equality.
+    nx, ny, nz, dx, V = 16, 16, 20, 5e-4, 300.0
+    kw = dict(mu=MU, D=DD, alpha=ALPHA, voltage_V=V, lateral_bc=o.LATERAL_ABSORBING, scheme=o.SCHEME_UPWIND)
+    let, b = 300.0, 1e-3
+    dt = o.dt_rule(dx, V, nz * dx, n_peak=o.peak_track_density([let], [b]), scheme=o.SCHEME_UPWIND)
+    P = 400
+    one = o.Oracle(nx, ny, nz, dx, dt, **kw)
+    one.deposit([0.5 * nx * dx], [0.5 * ny * dx], [let], [b])
+    one.step(P)
+    t1 = one.tallies()
+    assert t1.in_domain.sum() / t1.released.sum() < 1e-13      # a track's life is shorter than P
+    f1 = t1.f
+    assert 0.0 < f1 < 1.0 and t1.recombined > 0 and t1.lost_lateral.sum() > 0
+    n = 6
+    steps = np.arange(n, dtype=np.int64) * P
+    xs, ys = np.full(n, 0.5 * nx * dx), np.full(n, 0.5 * ny * dx)
+    train = o.Oracle(nx, ny, nz, dx, dt, **kw)
+    f_ss, stop, done = train.run_to_steady_state(xs, ys, np.full(n, let), np.full(n, b), steps, P, 1e-9, n * P)
+    assert stop == 0 and done == 2 * P
+    assert f_ss == pytest.approx(f1, rel=1e-11)
+
+
+def test_steady_state_runner_stops_at_the_step_limit():
+    # a window longer than the limit: no window runs, the limit is reported
+    O = o.Oracle(8, 8, 8, 5e-4, 1e-9, mu=MU, D=DD, alpha=ALPHA, voltage_V=100.0)
+    f_ss, stop, done = O.run_to_steady_state([], [], [], [], np.zeros(0, dtype=np.int64), 50, 1e-5, 40)
+    assert stop == 1 and done == 0 and math.isnan(f_ss)
