@@ -386,6 +386,26 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     t_kernel = k0.elapsed_time(k1) / 1e3 / nk
 
+    # the temporal-blocking variant (two steps per launch) on the same state,
+    # for the record of what the autotuner weighed
+    tb2 = None
+    try:
+        with torch.cuda.stream(stream):
+            sim2 = B.Simulation(w.nx, w.ny, w.nz, w.dx_cm, w.voltage_V, n_peak_cm3=npk, torch_state=True,
+                                kernel=B.IT_KERNEL_ZMARCH2)
+        B.it_deposit_tracks_device(sim2.h, ntr, d_tracks.data_ptr())
+        sim2.step(64)
+        torch.cuda.synchronize()
+        k0.record(stream)
+        sim2.step(nk)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        tb2 = {"kernel": "step_zmarch2_kernel (two steps per launch)", "launch": sim2.launch(),
+               "us_per_step": k0.elapsed_time(k1) * 1e3 / nk}
+        sim2.close()
+    except Exception as e:   # a grid the two-step kernel cannot tile
+        tb2 = {"unavailable": str(e)}
+
     # ---- end to end through the public API with host buffers ----
     def e2e_step():
         sim.reset()
@@ -433,17 +453,25 @@ def run_ours(args, ws, rank, local):
             "data": "synthetic",
             "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "dx_um": w.dx_cm * 1e4,
                        "tracks_per_pulse": ntr, "time_steps_per_step": seg, "voltage_V": w.voltage_V,
-                       "tallies": "f64", "kernel": "zmarch" if launch["kernel"] == B.IT_KERNEL_ZMARCH else "simple",
+                       "tallies": "f64", "kernel": {B.IT_KERNEL_ZMARCH: "zmarch", B.IT_KERNEL_ZMARCH2: "zmarch2"}.get(
+                           launch["kernel"], "simple"),
                        "launch": launch, "autotune_us_per_step": tune_us, "l2": "inputs larger than L2 (210 MB state read per time step)",
                        "parallelism": f"replicas{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         # two steps per launch read and write the state once per two steps:
+                         # 16 B per cell-update is then an effective figure
+                         "effective": launch["kernel"] == B.IT_KERNEL_ZMARCH2,
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "step_zmarch_kernel", "kernel_us": t_kernel * 1e6,
+                         "kernel": "step_zmarch2_kernel" if launch["kernel"] == B.IT_KERNEL_ZMARCH2 else "step_zmarch_kernel",
+                         "kernel_us": t_kernel * 1e6,
                          "bytes_per_launch": BYTES_PER_CELL_UPDATE * cells},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": ntr * 4 * 8,
                     "d2h_bytes_per_step": 17 * 8},
-            "gpu_launches": args.steps * (seg + 4),   # per step: 4 deposit kernels + seg step kernels
+            # per benchmark step: 4 deposit kernels + the step launches (two steps
+            # per launch with the two-step kernel, the odd one on the simple kernel)
+            "gpu_launches": args.steps * (4 + (seg // 2 + seg % 2 if launch["kernel"] == B.IT_KERNEL_ZMARCH2 else seg)),
+            "temporal_blocking_2": tb2,
             "clocks": clocks,
             "f_last": t.f,
             "roofline_continuous_512x512x256": cont,

@@ -204,7 +204,9 @@ int it_run_to_completion(it_ctx *ctx, double tol, int64_t max_steps,
  * *stop (may be NULL) 0 when the steady state ended the run and 1 when the
  * step limit did, *steps_done (may be NULL) the steps taken.  Returns
  * IT_EUNSTABLE if the state went non-finite; reaching the step limit is not
- * an error. */
+ * an error.  Windows in which no pair recombined and nothing was lost have
+ * f_ss = 1: two such windows in a row (sparse arrivals) meet the rule
+ * trivially. */
 int it_run_to_steady_state(it_ctx *ctx, int64_t window_steps, double tol, int64_t max_steps, double *f_ss,
                            int *stop, int64_t *steps_done);
 
