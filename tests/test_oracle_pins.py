@@ -443,6 +443,62 @@ def test_uniform_slab_follows_boag_two_voltage_method(u):
     assert t.f == pytest.approx(o.boag_2vm(u), abs=1e-2)
 
 
+def _run_to_completion(O, tol=1e-6, chunk=100, cap=200000):
+    while True:
+        O.step(chunk)
+        t = O.tallies()
+        if t.in_domain.sum() / t.released.sum() < tol or t.steps >= cap:
+            return t
+
+
+def test_f_converges_at_first_order_in_the_reaction_bound():
+    # The reaction-stability reading dt = min(dt_vN, kappa / (alpha n_peak)).
+    # Explicit recombination is first order in dt, so with the bound active
+    # successive halvings of kappa change f by half as much each time; from
+    # kappa = 0.25 a halving moves f by less than 1e-3.  On this dense field
+    # (LET up to 1000 keV/um) kappa = 0.5 moves f by about 2e-3, an error of
+    # about 4e-3 against dt -> 0.  A second-order or missing reaction term, or
+    # a bound that is not active, breaks the ratio.
+    nx, ny, nz, dx, V = 24, 24, 40, 5e-4, 200.0
+    tr = synth.uniform_tracks(9, 12, nx * dx, ny * dx, 1e-3, let="loguniform")
+    npk = o.peak_track_density(tr.let_keV_um, tr.b_cm)
+    fs = []
+    for kappa in (0.5, 0.25, 0.125):
+        dt = o.dt_rule(dx, V, nz * dx, MU, DD, ALPHA, n_peak=npk, kappa=kappa, scheme=o.SCHEME_UPWIND)
+        assert dt < o.dt_von_neumann(dx, V, nz * dx, MU, DD, scheme=o.SCHEME_UPWIND)   # the bound is active
+        O = o.Oracle(nx, ny, nz, dx, dt, mu=MU, D=DD, alpha=ALPHA, voltage_V=V, scheme=o.SCHEME_UPWIND)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        fs.append(_run_to_completion(O).f)
+    d1, d2 = fs[1] - fs[0], fs[2] - fs[1]
+    assert 0.0 < fs[0] < 1.0 and d1 > 0 and d2 > 0
+    assert 1.7 < d1 / d2 < 2.5
+    assert d2 < 1e-3 < d1
+
+
+def test_many_overlapping_low_let_tracks_follow_boag():
+    # Many proton-like tracks (LET ~4e-3 keV/um, spaced at b) released at
+    # once: initial recombination is negligible, the tracks merge into a
+    # nearly uniform charge density n = released / (Lx Ly d), and f follows
+    # Boag's pulsed-beam f = ln(1+u)/u with u = alpha n d^2 / ((mu+ + mu-) V)
+    # (P:211).  Track structure and the diffusion of the fronts are
+    # the residual.
+    nx, ny, nz, dx, V, b = 24, 24, 40, 5e-4, 200.0, 1e-3
+    d = nz * dx
+    g = (np.arange(12) + 0.5) * (nx * dx / 12)
+    xs, ys = [a.ravel() for a in np.meshgrid(g, g)]
+    u_target = 1.0
+    n = u_target * (MU[0] + MU[1]) * V / (ALPHA * d * d)
+    let = n * 34.0 * (nx * dx) * (ny * dx) / (xs.size * 1e7)
+    dt = o.dt_rule(dx, V, d, MU, DD, ALPHA, n_peak=o.peak_track_density([let], [b]))
+    O = o.Oracle(nx, ny, nz, dx, dt, mu=MU, D=DD, alpha=ALPHA, voltage_V=V)
+    O.deposit(xs, ys, np.full(xs.size, let), np.full(xs.size, b))
+    t = _run_to_completion(O)
+    n_rel = t.released[0] / ((nx * dx) * (ny * dx) * d)
+    u = o.boag_u(ALPHA, MU[0], MU[1], n_rel, d, V)
+    assert u == pytest.approx(u_target, rel=1e-6)
+    assert t.f == pytest.approx(o.boag_2vm(u), abs=2e-2)
+
+
 def test_upwind_stays_positive_where_lax_wendroff_undershoots():
     # With the recombination-bound dt the Courant number is small; the
     # upwind weights are all non-negative (6 s + c <= 1) and the explicit
