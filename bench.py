@@ -247,6 +247,11 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
     cell_updates = sum(sims[q]["nx"] * sims[q]["ny"] * sims[q]["nz"] * tal_all[q].steps for q in range(len(sims)))
     return {"sims": len(sims), "solves_per_s": len(sims) / t_all, "seconds": t_all, "step_launches": launches,
             "autotune_s": tune[0], "autotuned_us_per_step": tune[1],
+            # one batched step with every simulation active (the autotuner's best time): the
+            # per-step rate before simulations finish and the tail leaves SMs idle
+            "full_occupancy_Gcell_updates_per_s": sum(q["nx"] * q["ny"] * q["nz"] for q in sims) / tune[1] / 1e3,
+            "full_occupancy_hbm_frac": BYTES_PER_CELL_UPDATE * sum(q["nx"] * q["ny"] * q["nz"] for q in sims)
+                                       / tune[1] / 1e3 / hbm_peak()[0],
             "Gcell_updates_per_s": cell_updates / t_all / 1e9,
             "subset": n_subset, "subset_batched_solves_per_s": n_subset / t_bsub,
             "subset_plain_solves_per_s": n_subset / t_plain,
