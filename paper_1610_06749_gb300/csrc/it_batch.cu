@@ -20,6 +20,7 @@
 
 #include "it_device.cuh"
 #include "it_internal.cuh"
+#include "it_tma.cuh"
 
 namespace itk {
 
@@ -124,17 +125,18 @@ __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpre
 // hits: they are other threads' centres), and takes x-neighbours by warp
 // shuffle.  Same per-cell operation sequence as every other kernel.
 template <bool PERIODIC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__restrict__ tab,
                         const float *__restrict__ ip_all, const float *__restrict__ im_all,
                         float *__restrict__ op_all, float *__restrict__ om_all, double *__restrict__ slots) {
-    __shared__ double red[32 * 7];
+    __shared__ double wacc[8 * 8];   // per-warp FP64 tallies (tally q of warp w at w*8+q)
     __shared__ BatchSim S;
     __shared__ VecEntry E;
     if (threadIdx.x == 0) {
         E = tab[blockIdx.x];
         S = sims[E.sim];
     }
+    if (threadIdx.x < 64) wacc[threadIdx.x] = 0.0;
     __syncthreads();
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     const Coef<float> &c = S.cf;
@@ -142,7 +144,7 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
     float *out_[2] = {op_all + S.off, om_all + S.off};
     const int plane = nx * ny;
     const int ncol4 = nx >> 2;
-    const int t = threadIdx.x, lane = t & 31;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int ty = t / ncol4, c4 = t - (t / ncol4) * ncol4;
     const bool valid = ty < E.rows;
     const int yg = E.y0 + (valid ? ty : E.rows - 1);
@@ -157,21 +159,28 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
     const int row_r = yg * nx + (c4 == ncol4 - 1 ? 0 : x0 + 4);
     const bool zero_l = !PERIODIC && c4 == 0, zero_r = !PERIODIC && c4 == ncol4 - 1;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // warp-uniform: one FP32 partial per lane, reduced in FP64 (fixed order)
+    // into the warp's tally q
+    auto flush = [&](int q, float part) {
+        double v = (double)part;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) wacc[warp * 8 + q] += v;
+    };
     float4 prev[2], cur[2];
     for (int s = 0; s < 2; ++s) {
         prev[s] = E.z0 > 0 ? ldg4(in_[s] + (E.z0 - 1) * plane + row) : zero4;
         cur[s] = ldg4(in_[s] + E.z0 * plane + row);
     }
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    float rsum = 0.f;
+    float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f;
     int nacc = 0;
     for (int k = E.z0; k < E.z1; ++k) {
         const int pk = k * plane;
         float4 nxt[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) nxt[s] = k + 1 < nz ? ldg4(in_[s] + pk + plane + row) : zero4;
-        const float4 P = cur[0], M = cur[1];
-        const float4 rr = make_float4(P.x * M.x, P.y * M.y, P.z * M.z, P.w * M.w);
+        const float2 rxy = __fmul2_rn(make_float2(cur[0].x, cur[0].y), make_float2(cur[1].x, cur[1].y));
+        const float2 rzw = __fmul2_rn(make_float2(cur[0].z, cur[0].w), make_float2(cur[1].z, cur[1].w));
         float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -182,13 +191,8 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
             float r = __shfl_down_sync(0xffffffffu, n.x, 1);
             if (need_l) l = zero_l ? 0.f : __ldg(in_[s] + pk + row_l);
             if (need_r) r = zero_r ? 0.f : __ldg(in_[s] + pk + row_r);
-            const float4 zm = prev[s], zp = nxt[s];
-            const float w0 = c.w0[s], wx = c.wx[s], wy = c.wy[s], wzm = c.wzm[s], wzp = c.wzp[s], adt = c.adt;
-            float4 v;
-            v.x = upd7(n.x, l, n.y, u.x, d.x, zm.x, zp.x, rr.x, w0, wx, wy, wzm, wzp, adt);
-            v.y = upd7(n.y, n.x, n.z, u.y, d.y, zm.y, zp.y, rr.y, w0, wx, wy, wzm, wzp, adt);
-            v.z = upd7(n.z, n.y, n.w, u.z, d.z, zm.z, zp.z, rr.z, w0, wx, wy, wzm, wzp, adt);
-            v.w = upd7(n.w, n.z, r, u.w, d.w, zm.w, zp.w, rr.w, w0, wx, wy, wzm, wzp, adt);
+            const float4 v = upd7x4(n, l, r, u, d, prev[s], nxt[s], rxy, rzw, c.w0[s], c.wx[s], c.wy[s], c.wzm[s],
+                                    c.wzp[s], c.adt);
             if (valid) {
                 *reinterpret_cast<float4 *>(out_[s] + pk + row) = v;
                 if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
@@ -202,26 +206,37 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
             prev[s] = n;
             cur[s] = nxt[s];
         }
-        if (valid) rsum += (rr.x + rr.y) + (rr.z + rr.w);
-        if (++nacc == 32) { acc[0] += (double)rsum; rsum = 0.f; nacc = 0; }
-        if (k == 0) { acc[1] += (double)an[0]; acc[2] += (double)an[1]; }
-        if (k == nz - 1) { acc[3] += (double)an[0]; acc[4] += (double)an[1]; }
-        if (!PERIODIC) {
-            acc[5] += (double)lat[0] * c.latx_f[0];
-            acc[6] += (double)lat[1] * c.latx_f[1];
+        if (valid) rsum += (rxy.x + rxy.y) + (rzw.x + rzw.y);
+        if (!PERIODIC) { lsum0 += lat[0]; lsum1 += lat[1]; }
+        // FP32 partials over at most 32 planes, then FP64
+        if (++nacc == 32) {
+            flush(0, rsum);
+            rsum = 0.f;
+            if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); lsum0 = lsum1 = 0.f; }
+            nacc = 0;
         }
+        if (k == 0) { flush(1, an[0]); flush(2, an[1]); }
+        if (k == nz - 1) { flush(3, an[0]); flush(4, an[1]); }
     }
-    acc[0] += (double)rsum;
-    block_sum<7>(acc, red);
+    flush(0, rsum);
+    if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double acc[7];
+        for (int q = 0; q < 7; ++q) {
+            double v = 0.0;
+            for (int w = 0; w < 8; ++w) v += wacc[w * 8 + q];
+            acc[q] = v;
+        }
         double *sl = slots + (size_t)blockIdx.x * NT;
         sl[0] += acc[0] * c.rec_f;
         sl[1] += acc[1] * c.anode_f[0];
         sl[2] += acc[2] * c.anode_f[1];
         sl[3] += acc[3] * c.cathode_f[0];
         sl[4] += acc[4] * c.cathode_f[1];
-        sl[5] += acc[5];
-        sl[6] += acc[6];
+        // lateral faces: x and y weights are equal for dx = dy (latx_f == laty_f)
+        sl[5] += acc[5] * c.latx_f[0];
+        sl[6] += acc[6] * c.latx_f[1];
     }
 }
 
