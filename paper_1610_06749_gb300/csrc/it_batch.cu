@@ -125,7 +125,7 @@ __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpre
 // hits: they are other threads' centres), and takes x-neighbours by warp
 // shuffle.  Same per-cell operation sequence as every other kernel.
 template <bool PERIODIC>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
 step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__restrict__ tab,
                         const float *__restrict__ ip_all, const float *__restrict__ im_all,
                         float *__restrict__ op_all, float *__restrict__ om_all, double *__restrict__ slots) {
@@ -167,18 +167,19 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) wacc[warp * 8 + q] += v;
     };
-    float4 prev[2], cur[2];
+    float4 prev[2], cur[2], nxt[2];
     for (int s = 0; s < 2; ++s) {
         prev[s] = E.z0 > 0 ? ldg4(in_[s] + (E.z0 - 1) * plane + row) : zero4;
         cur[s] = ldg4(in_[s] + E.z0 * plane + row);
+        nxt[s] = E.z0 + 1 < nz ? ldg4(in_[s] + (E.z0 + 1) * plane + row) : zero4;
     }
     float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f;
     int nacc = 0;
     for (int k = E.z0; k < E.z1; ++k) {
         const int pk = k * plane;
-        float4 nxt[2];
+        float4 nn[2];   // two planes ahead: more loads in flight per thread
 #pragma unroll
-        for (int s = 0; s < 2; ++s) nxt[s] = k + 1 < nz ? ldg4(in_[s] + pk + plane + row) : zero4;
+        for (int s = 0; s < 2; ++s) nn[s] = k + 2 < nz ? ldg4(in_[s] + pk + 2 * plane + row) : zero4;
         const float2 rxy = __fmul2_rn(make_float2(cur[0].x, cur[0].y), make_float2(cur[1].x, cur[1].y));
         const float2 rzw = __fmul2_rn(make_float2(cur[0].z, cur[0].w), make_float2(cur[1].z, cur[1].w));
         float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
@@ -205,6 +206,7 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
             }
             prev[s] = n;
             cur[s] = nxt[s];
+            nxt[s] = nn[s];
         }
         if (valid) rsum += (rxy.x + rxy.y) + (rzw.x + rzw.y);
         if (!PERIODIC) { lsum0 += lat[0]; lsum1 += lat[1]; }
