@@ -258,7 +258,9 @@ __global__ void batch_fold_kernel(const int *__restrict__ first, const int *__re
     acc[(size_t)sim_of[a] * NT + q] += s;
 }
 
-// Per-entry sums of n+ and n- (FP64), for the in-domain charge.
+// Per-entry sums of n+ and n- for the in-domain charge: FP32 partials over
+// at most 32 cells per thread, then FP64 (once per 32 cells, outside the
+// per-cell loop: FP64 arithmetic is slow on this GPU).
 __global__ void __launch_bounds__(256)
 batch_monitor_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restrict__ tab,
                      const float *__restrict__ ip_all, const float *__restrict__ im_all, double *__restrict__ mon) {
@@ -267,9 +269,16 @@ batch_monitor_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__rest
     const long long off = sims[E.sim].off;
     const long long nxs = sims[E.sim].nx;
     double v[2] = {0.0, 0.0};
-    for (size_t idx = (size_t)(E.begin * nxs) + threadIdx.x; idx < (size_t)(E.end * nxs); idx += blockDim.x) {
-        v[0] += (double)ip_all[off + idx];
-        v[1] += (double)im_all[off + idx];
+    const size_t end = (size_t)(E.end * nxs);
+    size_t idx = (size_t)(E.begin * nxs) + threadIdx.x;
+    while (idx < end) {
+        float a = 0.f, b = 0.f;
+        for (int j = 0; j < 32 && idx < end; ++j, idx += blockDim.x) {
+            a += ip_all[off + idx];
+            b += im_all[off + idx];
+        }
+        v[0] += (double)a;
+        v[1] += (double)b;
     }
     block_sum<2>(v, red);
     if (threadIdx.x == 0) {

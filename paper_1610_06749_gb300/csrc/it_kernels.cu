@@ -120,28 +120,32 @@ int launch_step_simple_raw_f32(const float *ip, const float *im, float *op, floa
 // ---------------------------------------------------------------------------
 // monitor: in-domain ions and extreme densities of the current state
 // ---------------------------------------------------------------------------
-// Per-thread accumulation of one cell of each species: FP32 (or FP64)
-// partial sums over at most 32 cells, then FP64.
+// Per-thread accumulation of one cell of each species into T partial sums
+// and extremes; the partials are moved to FP64 by flush(), which callers run
+// once per at most 32 cells outside the per-cell code (FP64 is slow on this
+// GPU: an FP64 add in the per-cell path, even a predicated one, would bound
+// the kernel).
 template <typename T>
 struct MonAcc {
     double sum[2] = {0.0, 0.0};
     T part[2] = {0, 0};
-    int np = 0;
     T mn[2] = {(T)INFINITY, (T)INFINITY}, mx[2] = {(T)-INFINITY, (T)-INFINITY};
     __device__ __forceinline__ void add(T a, T b) {
         part[0] += a; part[1] += b;          // a NaN propagates into the sums
         mn[0] = a < mn[0] ? a : mn[0]; mn[1] = b < mn[1] ? b : mn[1];
         mx[0] = a > mx[0] ? a : mx[0]; mx[1] = b > mx[1] ? b : mx[1];
-        if (++np == 32) {
-            sum[0] += (double)part[0]; sum[1] += (double)part[1];
-            part[0] = part[1] = 0; np = 0;
-        }
+    }
+    __device__ __forceinline__ void flush() {
+        sum[0] += (double)part[0]; sum[1] += (double)part[1];
+        part[0] = part[1] = 0;
     }
 };
 
 // In-domain sums and extremes of both species, one row of NM values per CTA.
-// FP32 states on 16-byte boundaries are read as float4 (four loads of each
-// species in flight per thread); other cells are read one by one.
+// FP32 states on 16-byte boundaries are read as float4, four loads of each
+// species in flight per thread, and summed in FP32 over 32 cells (two
+// rounds of four float4) before FP64; other cells are read one by one and
+// summed in T over up to 32 cells.
 template <typename T>
 __global__ void __launch_bounds__(256)
 monitor_kernel(const T *__restrict__ ip, const T *__restrict__ im, size_t total, double vol,
@@ -158,27 +162,42 @@ monitor_kernel(const T *__restrict__ ip, const T *__restrict__ im, size_t total,
         const float4 *p4 = reinterpret_cast<const float4 *>(ip);
         const float4 *m4 = reinterpret_cast<const float4 *>(im);
         size_t q = tid;
-        for (; q + 3 * nthr < n4; q += 4 * nthr) {
-            float4 a[4], b[4];
+        bool more = true;
+        while (more) {
+            // one round: up to two groups of four float4 per species (32 cells)
+            for (int g = 0; g < 2; ++g) {
+                if (q + 3 * nthr >= n4) { more = false; break; }
+                float4 a[4], b[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a[u] = __ldcs(p4 + q + u * nthr);
-                b[u] = __ldcs(m4 + q + u * nthr);
-            }
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = __ldcs(p4 + q + u * nthr);
+                    b[u] = __ldcs(m4 + q + u * nthr);
+                }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                acc.add(a[u].x, b[u].x); acc.add(a[u].y, b[u].y);
-                acc.add(a[u].z, b[u].z); acc.add(a[u].w, b[u].w);
+                for (int u = 0; u < 4; ++u) {
+                    acc.add(a[u].x, b[u].x); acc.add(a[u].y, b[u].y);
+                    acc.add(a[u].z, b[u].z); acc.add(a[u].w, b[u].w);
+                }
+                q += 4 * nthr;
             }
+            acc.flush();
         }
-        for (; q < n4; q += nthr) {
+        for (; q < n4; q += nthr) {   // fewer than four float4 left per thread
             const float4 a = __ldcs(p4 + q), b = __ldcs(m4 + q);
             acc.add(a.x, b.x); acc.add(a.y, b.y); acc.add(a.z, b.z); acc.add(a.w, b.w);
         }
+        acc.flush();
         done = n4 * 4;
     }
-    for (size_t idx = done + tid; idx < total; idx += nthr) acc.add(ip[idx], im[idx]);
-    double sum[2] = {acc.sum[0] + (double)acc.part[0], acc.sum[1] + (double)acc.part[1]};
+    {
+        int n = 0;
+        for (size_t idx = done + tid; idx < total; idx += nthr) {
+            acc.add(ip[idx], im[idx]);
+            if (++n == 32) { acc.flush(); n = 0; }
+        }
+        acc.flush();
+    }
+    double sum[2] = {acc.sum[0], acc.sum[1]};
     double mn[2] = {(double)acc.mn[0], (double)acc.mn[1]}, mx[2] = {(double)acc.mx[0], (double)acc.mx[1]};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -411,8 +430,10 @@ deposit_plane_kernel(const double *__restrict__ tr, const double *__restrict__ w
 
 // n += plane on every z plane.  Thread = V adjacent columns (float4 when the
 // state is FP32 and nx % 4 == 0) over a chunk of DEP_KCHUNK planes
-// (blockIdx.y); columns the deposit did not reach are skipped.  Each cell is
-// rounded as T(double(n) + plane) in every variant.
+// (blockIdx.y); columns the deposit did not reach are skipped.  FP32 states
+// add the plane value rounded to FP32 (n + float(plane), one FP32 addition:
+// FP64 arithmetic is slow on this GPU and the two roundings stay within an
+// ulp of the exact sum); FP64 states add it exactly in FP64.
 constexpr int DEP_KCHUNK = 8;
 template <typename T, int V>
 __global__ void __launch_bounds__(256)
@@ -430,22 +451,29 @@ deposit_apply_kernel(T *__restrict__ p, T *__restrict__ m, const double *__restr
     if (!any) return;   // x + 0 == x: nothing to write
     const int k0 = blockIdx.y * DEP_KCHUNK, k1 = min(nz, k0 + DEP_KCHUNK);
     if constexpr (V == 4) {
+        const float4 af = make_float4(__double2float_rn(a[0]), __double2float_rn(a[1]), __double2float_rn(a[2]),
+                                      __double2float_rn(a[3]));
         float4 *p4 = reinterpret_cast<float4 *>(p), *m4 = reinterpret_cast<float4 *>(m);
         for (int k = k0; k < k1; ++k) {
             const size_t i4 = ((size_t)k * plane_n + c0) / 4;
             float4 x = p4[i4], y = m4[i4];
-            x.x = (float)((double)x.x + a[0]); x.y = (float)((double)x.y + a[1]);
-            x.z = (float)((double)x.z + a[2]); x.w = (float)((double)x.w + a[3]);
-            y.x = (float)((double)y.x + a[0]); y.y = (float)((double)y.y + a[1]);
-            y.z = (float)((double)y.z + a[2]); y.w = (float)((double)y.w + a[3]);
+            x.x = __fadd_rn(x.x, af.x); x.y = __fadd_rn(x.y, af.y); x.z = __fadd_rn(x.z, af.z); x.w = __fadd_rn(x.w, af.w);
+            y.x = __fadd_rn(y.x, af.x); y.y = __fadd_rn(y.y, af.y); y.z = __fadd_rn(y.z, af.z); y.w = __fadd_rn(y.w, af.w);
             p4[i4] = x;
             m4[i4] = y;
+        }
+    } else if constexpr (sizeof(T) == 4) {
+        const float af = __double2float_rn(a[0]);
+        for (int k = k0; k < k1; ++k) {
+            const size_t idx = (size_t)k * plane_n + c0;
+            p[idx] = __fadd_rn(p[idx], af);
+            m[idx] = __fadd_rn(m[idx], af);
         }
     } else {
         for (int k = k0; k < k1; ++k) {
             const size_t idx = (size_t)k * plane_n + c0;
-            p[idx] = (T)((double)p[idx] + a[0]);
-            m[idx] = (T)((double)m[idx] + a[0]);
+            p[idx] += a[0];
+            m[idx] += a[0];
         }
     }
 }
