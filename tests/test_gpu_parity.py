@@ -299,6 +299,24 @@ def test_pulsed_256x256x400_full_size(V):
         compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
 
 
+def test_pulsed_full_size_in_the_autotuned_launch_shape():
+    # the shape bench.py times: the autotuner's pick on the deposited pulse,
+    # then the full arrays against the oracle
+    w = synth.pulsed_256x256x400(200.0)
+    tr = synth.pulsed_tracks(w)
+    g, O = make_pair(w.nx, w.ny, w.nz, w.dx_cm, w.voltage_V, tr)
+    with g:
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        g.autotune(trial_steps=4, force=True)
+        assert g.launch()["kernel"] in (B.IT_KERNEL_ZMARCH, B.IT_KERNEL_ZMARCH2)
+        g.step(4)
+        O.step(4)
+        for s in range(2):
+            assert_density_close(g.density(s), O.density(s), 1e-4)
+        compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
+
+
 def test_two_step_kernel_full_size_bitwise_and_against_the_oracle():
     # the benchmark workload on the two-step kernel: bitwise the one-step
     # kernel after 40 steps (odd counts included), the oracle after 3
