@@ -42,6 +42,38 @@ FALLBACK_HBM_GBS = 6800.0
 PROFILE = os.path.join(ROOT, "profiles", "step_zmarch_pulsed_256x256x400.json")
 
 
+REPLICA_SEED_STRIDE = 7919
+
+
+def replica_seed(seed, rank):
+    """Seed of a rank's replica: every rank runs its own independent pulse
+    (weak scaling, no data-path collective)."""
+    return seed + REPLICA_SEED_STRIDE * rank
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device=None):
+    """The largest x over the ranks: the job's time is its slowest rank's.
+    device: where the reduction tensor lives (cuda for NCCL, cpu for gloo)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds):
+    """Units all ranks processed, per second of the slowest rank."""
+    return units_per_rank * ws / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -320,7 +352,7 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
 
     w = synth.pulsed_256x256x400(args.voltage)
-    w.seed += 7919 * rank                          # independent replica per rank
+    w.seed = replica_seed(w.seed, rank)            # independent replica per rank
     tracks = synth.pulsed_tracks(w)
     ntr = len(tracks)
     npk = B.it_peak_density(tracks.let_keV_um, tracks.b_cm)
@@ -344,18 +376,8 @@ def run_ours(args, ws, rank, local):
     launch = sim.launch()
     cells, seg = w.cells, args.seg
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     def maxover(x):
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([x], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        return max_over_ranks(x, ws, dev)
 
     def dev_step():
         sim.reset()
@@ -366,7 +388,7 @@ def run_ours(args, ws, rank, local):
     for _ in range(args.warmup):
         dev_step()
     torch.cuda.synchronize()
-    barrier()
+    barrier(ws)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -375,7 +397,7 @@ def run_ours(args, ws, rank, local):
             dev_step()
         ev1.record(stream)
         torch.cuda.synchronize()
-    barrier()
+    barrier(ws)
     torch.cuda.synchronize()
     t_dev = maxover(ev0.elapsed_time(ev1) / 1e3)
     clocks = clk.summary()
@@ -419,16 +441,16 @@ def run_ours(args, ws, rank, local):
         return sim.tallies()                                                    # D2H of the tallies
     for _ in range(max(1, args.warmup)):
         e2e_step()
-    barrier()
+    barrier(ws)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         t = e2e_step()
     t_e2e = maxover(time.perf_counter() - t0)
-    barrier()
+    barrier(ws)
 
     total_updates = cells * seg * args.steps * ws
-    value = total_updates / t_dev / 1e9
-    e2e_value = total_updates / t_e2e / 1e9
+    value = whole_job_rate(cells * seg * args.steps, ws, t_dev) / 1e9
+    e2e_value = whole_job_rate(cells * seg * args.steps, ws, t_e2e) / 1e9
     peak, peak_kind = hbm_peak()
     achieved = BYTES_PER_CELL_UPDATE * cells / t_kernel / 1e9
     traffic = ncu_traffic()
