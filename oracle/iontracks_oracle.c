@@ -14,12 +14,17 @@
  *     track parallel to the field that spans the gap, so the released charge is
  *     N0 * l (Eq. created) minus whatever falls outside an absorbing domain.
  *   - Transport: the continuity equations of Eq. (cont_eq)/(theEquation) with a
- *     uniform field E = V/d along +z (no space-charge term), discretised as in
+ *     uniform external field E = V/d along +z, discretised as in
  *     the Appendix: forward-Euler time derivative, the blended
  *     backward/central first derivative weighted by c = mu E dt/dz, and the
  *     3-point second derivative per axis.  The upwind side follows each
  *     species' own drift direction (reading).  Recombination -alpha n+ n- is
  *     taken from the old time level.
+ *   - Space charge (optional, off by default): the term -/+ mu n div E of Eq.
+ *     (theEquation) with div E from the Maxwell-Gauss equation,
+ *     div E = q/eps0 (n+ - n-), also from the old time level; its net change
+ *     of each species is tallied (the term as printed does not conserve
+ *     charge).
  *   - Boundaries: n = 0 on the electrode planes (Sec. Methods, boundary
  *     conditions) realised as ghost cells k = -1 and k = nz that hold zero.
  *     Lateral faces are periodic or absorbing (zero ghosts) -- the paper only
@@ -56,8 +61,15 @@ typedef struct {
     double *plane_work;   /* per-plane partial sums */
     double released[2], col_anode[2], col_cathode[2], lost_lateral[2];
     double recombined;
+    int space_charge;     /* 1: include the -/+ mu n div E term */
+    double sc_added[2];   /* ions added to each species by that term (negative: removed) */
     int64_t steps;
 } orc_state;
+
+/* Elementary charge (C) and vacuum permittivity (F/cm): div E = Q/EPS0 (n+ - n-)
+ * with n in ions/cm^3 gives V/cm^2. */
+static const double ORC_Q = 1.602176634e-19;
+static const double ORC_EPS0 = 8.8541878128e-14;
 
 static inline size_t pidx(const orc_state *S, int i, int j, int k) {
     return ((size_t)(k + 1) * (size_t)(S->ny + 2) + (size_t)(j + 1)) * (size_t)(S->nx + 2) + (size_t)(i + 1);
@@ -171,7 +183,7 @@ static inline double at(const orc_state *S, const double *a, int i, int j, int k
 
 /* The right-hand side of the discretised Eq. (theEquation) at one cell,
  * returned as the new value n^{l+1}.  sigma = +1 for n+, -1 for n-. */
-static double update_cell(const orc_state *S, int s, int i, int j, int k, double rec) {
+static double update_cell(const orc_state *S, int s, int i, int j, int k, double rec, double divE) {
     const double *a = S->n[s];
     const double dx = S->dx, dt = S->dt;
     double n0 = at(S, a, i, j, k);
@@ -189,7 +201,9 @@ static double update_cell(const orc_state *S, int s, int i, int j, int k, double
     double central = (zp - zm) / (2.0 * dx);
     double upwind = (v >= 0.0) ? (n0 - zm) / dx : (zp - n0) / dx;
     double dndz = (S->scheme == 0) ? c * upwind + (1.0 - c) * central : upwind;
-    return n0 + dt * (S->D[s] * lap - v * dndz - rec);
+    /* space charge: -/+ mu n div E (zero unless enabled) */
+    double sc = sigma * S->mu[s] * n0 * divE;
+    return n0 + dt * (S->D[s] * lap - v * dndz - rec - sc);
 }
 
 /* One explicit time step of both species with tallies. */
@@ -211,15 +225,20 @@ void orc_step(orc_state *S) {
                 if (nghost == 0) {
                     double np = S->n[0][pidx(S, i, j, k)], nm = S->n[1][pidx(S, i, j, k)];
                     double rec = S->alpha * (np * nm);   /* symmetric in n+, n- */
+                    double divE = S->space_charge ? (ORC_Q / ORC_EPS0) * (np - nm) : 0.0;
                     for (int s = 0; s < 2; ++s)
-                        S->nn[s][pidx(S, i, j, k)] = update_cell(S, s, i, j, k, rec);
+                        S->nn[s][pidx(S, i, j, k)] = update_cell(S, s, i, j, k, rec, divE);
                     w[0] += S->alpha * S->dt * np * nm * vol;
+                    if (S->space_charge) {
+                        w[7] -= S->dt * S->mu[0] * np * divE * vol;   /* n+: -mu+ n+ div E */
+                        w[8] += S->dt * S->mu[1] * nm * divE * vol;   /* n-: +mu- n- div E */
+                    }
                 } else if (nghost == 1) {
                     /* a ghost cell next to the domain: what the update would
                      * move into it leaves the domain through that face */
                     if (!ghost_z && !absorbing) continue;   /* periodic copy */
                     for (int s = 0; s < 2; ++s) {
-                        double out = update_cell(S, s, i, j, k, 0.0) * vol;
+                        double out = update_cell(S, s, i, j, k, 0.0, 0.0) * vol;
                         if (ghost_z) w[(k < 0 ? 1 : 3) + s] += out;   /* 1,2 anode; 3,4 cathode */
                         else w[5 + s] += out;                         /* lateral */
                     }
@@ -227,15 +246,16 @@ void orc_step(orc_state *S) {
             }
         }
     }
-    double rec = 0, ca[2] = {0, 0}, cc[2] = {0, 0}, ll[2] = {0, 0};
+    double rec = 0, ca[2] = {0, 0}, cc[2] = {0, 0}, ll[2] = {0, 0}, sa[2] = {0, 0};
     for (int k = 0; k < nz + 2; ++k) {
         double *w = W + (size_t)k * 16;
         rec += w[0];
-        for (int s = 0; s < 2; ++s) { ca[s] += w[1 + s]; cc[s] += w[3 + s]; ll[s] += w[5 + s]; }
+        for (int s = 0; s < 2; ++s) { ca[s] += w[1 + s]; cc[s] += w[3 + s]; ll[s] += w[5 + s]; sa[s] += w[7 + s]; }
     }
     S->recombined += rec;
     for (int s = 0; s < 2; ++s) {
         S->col_anode[s] += ca[s]; S->col_cathode[s] += cc[s]; S->lost_lateral[s] += ll[s];
+        S->sc_added[s] += sa[s];
         double *t = S->n[s]; S->n[s] = S->nn[s]; S->nn[s] = t;
     }
     S->steps += 1;
@@ -277,6 +297,15 @@ void orc_tallies(const orc_state *S, double *out10) {
     out10[9] = (double)S->steps;
 }
 
+/* Space-charge term on (1) or off (0). */
+void orc_set_space_charge(orc_state *S, int on) { S->space_charge = on ? 1 : 0; }
+
+/* Ions added to each species by the space-charge term so far (negative: removed). */
+void orc_space_charge(const orc_state *S, double *out2) {
+    out2[0] = S->sc_added[0];
+    out2[1] = S->sc_added[1];
+}
+
 /* Copy one species' interior densities to dst laid out [nz][ny][nx]. */
 void orc_get_density(const orc_state *S, int s, double *dst) {
     const int nx = S->nx, ny = S->ny, nz = S->nz;
@@ -304,6 +333,7 @@ void orc_set_density(orc_state *S, const double *plus, const double *minus) {
                 }
         S->released[s] = sum * vol;
         S->col_anode[s] = S->col_cathode[s] = S->lost_lateral[s] = 0;
+        S->sc_added[s] = 0;
     }
     S->recombined = 0;
     S->steps = 0;

@@ -63,6 +63,8 @@ def _load():
         lib.orc_tallies.argtypes = [p, dp]
         lib.orc_get_density.argtypes = [p, i, dp]
         lib.orc_set_density.argtypes = [p, dp, dp]
+        lib.orc_set_space_charge.argtypes = [p, i]
+        lib.orc_space_charge.argtypes = [p, dp]
         _lib = lib
     return _lib
 
@@ -82,6 +84,7 @@ class Tallies:
     steps: int
     n_min: np.ndarray
     n_max: np.ndarray
+    space_charge: np.ndarray = None   # [2] ions added by the space-charge term (negative: removed)
 
     @property
     def collected(self) -> np.ndarray:
@@ -100,7 +103,7 @@ class Oracle:
 
     def __init__(self, nx, ny, nz, dx_cm, dt_s, mu=(1.73, 1.87), D=(0.037, 0.037),
                  alpha=1.6e-6, voltage_V=200.0, lateral_bc=LATERAL_PERIODIC,
-                 scheme=SCHEME_LAX_WENDROFF, W_eV=34.0):
+                 scheme=SCHEME_LAX_WENDROFF, W_eV=34.0, space_charge=False):
         lib = _load()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.dx, self.dt = float(dx_cm), float(dt_s)
@@ -112,6 +115,7 @@ class Oracle:
                                  float(alpha), self.E, int(lateral_bc), int(scheme))
         if not self._h:
             raise ValueError("oracle: invalid grid or step")
+        lib.orc_set_space_charge(self._h, 1 if space_charge else 0)
 
     def close(self):
         if self._h:
@@ -188,10 +192,12 @@ class Oracle:
         ind = np.zeros(2)
         mm = np.zeros(4)
         lib.orc_in_domain(self._h, _dptr(ind), _dptr(mm))
+        sc = np.zeros(2)
+        lib.orc_space_charge(self._h, _dptr(sc))
         return Tallies(released=t[0:2].copy(), collected_anode=t[2:4].copy(),
                        collected_cathode=t[4:6].copy(), lost_lateral=t[6:8].copy(),
                        in_domain=ind, recombined=float(t[8]), steps=int(t[9]),
-                       n_min=mm[[0, 2]].copy(), n_max=mm[[1, 3]].copy())
+                       n_min=mm[[0, 2]].copy(), n_max=mm[[1, 3]].copy(), space_charge=sc)
 
     def density(self, species: int) -> np.ndarray:
         out = np.empty((self.nz, self.ny, self.nx), dtype=np.float64)
@@ -244,12 +250,22 @@ def peak_track_density(let_keV_um, b_cm, W_eV=34.0) -> float:
     return float(np.max(N0 / (math.pi * b * b)))
 
 
+# Elementary charge (C) over the vacuum permittivity (F/cm), V cm: the
+# Maxwell-Gauss equation div E = q/eps0 (n+ - n-) with n in ions/cm^3.
+Q_OVER_EPS0 = 1.602176634e-19 / 8.8541878128e-14
+
+
 def dt_rule(dx_cm, voltage_V, gap_cm, mu=(1.73, 1.87), D=(0.037, 0.037), alpha=1.6e-6,
-            n_peak=0.0, cfl_safety=1.0, kappa=0.5, scheme=SCHEME_LAX_WENDROFF) -> float:
-    """dt = min(cfl_safety * dt_vN, kappa / (alpha n_peak))."""
+            n_peak=0.0, cfl_safety=1.0, kappa=0.5, scheme=SCHEME_LAX_WENDROFF, space_charge=False) -> float:
+    """dt = min(cfl_safety * dt_vN, kappa / (alpha n_peak)), and with the
+    space-charge term also kappa / (max(mu) q/eps0 n_peak): the term decays a
+    lone species at the rate mu q/eps0 n, resolved the same way as
+    recombination."""
     dt = cfl_safety * dt_von_neumann(dx_cm, voltage_V, gap_cm, mu, D, scheme)
     if alpha > 0 and n_peak > 0:
         dt = min(dt, kappa / (alpha * n_peak))
+    if space_charge and n_peak > 0:
+        dt = min(dt, kappa / (max(mu) * Q_OVER_EPS0 * n_peak))
     return dt
 
 

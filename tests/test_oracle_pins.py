@@ -560,3 +560,72 @@ def test_steady_state_runner_stops_at_the_step_limit():
     O = o.Oracle(8, 8, 8, 5e-4, 1e-9, mu=MU, D=DD, alpha=ALPHA, voltage_V=100.0)
     f_ss, stop, done = O.run_to_steady_state([], [], [], [], np.zeros(0, dtype=np.int64), 50, 1e-5, 40)
     assert stop == 1 and done == 0 and math.isnan(f_ss)
+
+
+# --------------------------------------------------------------------------
+# space-charge term of Eq. (theEquation): -/+ mu n div E, div E = q/eps0 (n+ - n-)
+# --------------------------------------------------------------------------
+Q_EPS0 = 1.602176634e-19 / 8.8541878128e-14   # retyped from CODATA, not from the oracle
+
+
+@pytest.mark.parametrize("species", [0, 1])
+def test_space_charge_of_a_lone_species_follows_its_recurrence(species):
+    # One species, uniform, no field, no diffusion, no recombination: each
+    # cell obeys n <- n - dt mu q/eps0 n^2 exactly (the cloud repels itself;
+    # for n- the sign of the term and of div E both flip), tending to
+    # n0 / (1 + mu q/eps0 n0 t).  A wrong sign, species or coefficient fails.
+    n0, dt, steps = 4e12, 2e-10, 40
+    mu = MU[species]
+    O = o.Oracle(3, 3, 3, 5e-4, dt, mu=MU, D=(0.0, 0.0), alpha=0.0, voltage_V=0.0, space_charge=True)
+    f = np.full((3, 3, 3), n0)
+    z = np.zeros((3, 3, 3))
+    O.set_density(f, z) if species == 0 else O.set_density(z, f)
+    n = n0
+    for _ in range(steps):
+        n = n - dt * mu * Q_EPS0 * n * n
+    O.step(steps)
+    got = O.density(species)
+    assert np.allclose(got, n, rtol=1e-13, atol=0)
+    assert np.all(O.density(1 - species) == 0.0)
+    t = O.tallies()
+    vol = (5e-4) ** 3 * 27
+    assert t.space_charge[species] == pytest.approx((n - n0) * vol, rel=1e-12)
+    cont = n0 / (1.0 + mu * Q_EPS0 * n0 * dt * steps)
+    assert n == pytest.approx(cont, rel=0.1) and abs(n - cont) / n0 < mu * Q_EPS0 * n0 * dt * 2
+
+
+def test_space_charge_leaves_a_neutral_plasma_alone():
+    # n+ = n- everywhere: div E = 0, so with no transport and no recombination
+    # nothing changes, bitwise
+    O = o.Oracle(3, 3, 3, 5e-4, 1e-9, mu=MU, D=(0.0, 0.0), alpha=0.0, voltage_V=0.0, space_charge=True)
+    f = np.full((3, 3, 3), 3e12)
+    O.set_density(f, f)
+    O.step(10)
+    assert np.array_equal(O.density(0), f) and np.array_equal(O.density(1), f)
+    assert np.all(O.tallies().space_charge == 0.0)
+
+
+def test_space_charge_conservation_and_proton_invariance():
+    # With the term on, the balance closes with its tally:
+    # released + added = in domain + collected + lost + recombined.  At a
+    # proton-like LET the term changes f by less than 1e-4.
+    nx, ny, nz, dx, V = 16, 16, 20, 5e-4, 200.0
+    for let, check_f in ((300.0, False), (2e-3, True)):
+        npk = o.peak_track_density([let], [1e-3])
+        dt = o.dt_rule(dx, V, nz * dx, MU, DD, ALPHA, n_peak=npk, scheme=o.SCHEME_UPWIND, space_charge=True)
+        fs = []
+        for sc in (True, False):
+            O = o.Oracle(nx, ny, nz, dx, dt, mu=MU, D=DD, alpha=ALPHA, voltage_V=V,
+                         lateral_bc=o.LATERAL_ABSORBING, scheme=o.SCHEME_UPWIND, space_charge=sc)
+            O.deposit([0.5 * nx * dx], [0.5 * ny * dx], [let], [1e-3])
+            O.step(150)
+            t = O.tallies()
+            for s in range(2):
+                lhs = t.released[s] + t.space_charge[s]
+                rhs = t.in_domain[s] + t.collected[s] + t.lost_lateral[s] + t.recombined
+                assert lhs == pytest.approx(rhs, rel=1e-12)
+            if sc and not check_f:
+                assert t.space_charge[0] < 0 and abs(t.space_charge[0]) > 1e-6 * t.released[0]
+            fs.append(t.f)
+        if check_f:
+            assert abs(fs[0] - fs[1]) < 1e-4
