@@ -98,7 +98,7 @@ def hbm_peak():
 
 def kernel_sha():
     h = hashlib.sha256()
-    for name in ("it_zmarch.cu", "it_device.cuh", "it_internal.cuh"):
+    for name in ("it_zmarch.cu", "it_tma.cuh", "it_device.cuh", "it_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1610_06749_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

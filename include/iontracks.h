@@ -93,6 +93,11 @@ typedef struct {
     double cfl_safety;      /* automatic dt = cfl_safety * dt_vN (default 1) */
     double react_kappa;     /* automatic dt <= react_kappa / (alpha n_peak) (default 0.5) */
     double n_peak_cm3;      /* peak density for that bound; 0 disables it */
+    int32_t space_charge;   /* 1: include the space-charge term of Eq. (theEquation),
+                               -/+ mu n div E with div E = q/eps0 (n+ - n-) (Maxwell-Gauss),
+                               from the old level; the automatic dt then also satisfies
+                               dt <= react_kappa / (max mu q/eps0 n_peak).  Default 0 */
+    int32_t reserved;       /* 0 */
 } it_params;
 
 typedef struct {
@@ -107,6 +112,10 @@ typedef struct {
     double dt_s;                 /* time step */
     int64_t steps;               /* steps taken */
     double n_min[2], n_max[2];   /* extreme densities of the current state */
+    double space_charge[2];      /* ions added to each species by the space-charge term
+                                    (negative: removed; 0 when it is off).  The balance is
+                                    released + space_charge = in_domain + collected
+                                    + lost_lateral + recombined */
 } it_tallies_t;
 
 /* Library version string (static storage). */
@@ -400,10 +409,10 @@ int it_mlp_destroy(it_mlp *net);
  * dev_tallies7: 7 device doubles that receive this step's recombined ion
  * pairs, anode +/-, cathode +/- and lateral +/- ions (the same quantities
  * it_tallies accumulates).  g, dx, dt and p as for it_create (p->precision
- * must be IT_FP32; dt must be given and within Eq. (vNeum)).  Enqueued on
+ * must be IT_FP32, p->space_charge 0; dt must be given and within Eq. (vNeum)).  Enqueued on
  * `stream` (a cudaStream_t, NULL = the legacy default stream).
  * The per-block tally partials live in one static device array of
- * IT_NOALLOC_MAX_BLOCKS x 8 doubles (128 KiB on each device that loads the
+ * IT_NOALLOC_MAX_BLOCKS x 10 doubles (160 KiB on each device that loads the
  * library, kept until exit); a device that would need more blocks is
  * rejected with IT_EINVAL.  The first call on a device looks up the array's
  * address (make it before any stream capture).  All calls share the array

@@ -42,7 +42,7 @@ class it_params(ctypes.Structure):
                 ("W_eV", ctypes.c_double), ("gap_cm", ctypes.c_double), ("voltage_V", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("lateral_bc", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("cfl_safety", ctypes.c_double), ("react_kappa", ctypes.c_double),
-                ("n_peak_cm3", ctypes.c_double)]
+                ("n_peak_cm3", ctypes.c_double), ("space_charge", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class it_tallies_t(ctypes.Structure):
@@ -50,7 +50,8 @@ class it_tallies_t(ctypes.Structure):
                 ("collected_cathode", ctypes.c_double * 2), ("lost_lateral", ctypes.c_double * 2),
                 ("in_domain", ctypes.c_double * 2), ("recombined", ctypes.c_double), ("f", ctypes.c_double),
                 ("t_s", ctypes.c_double), ("dt_s", ctypes.c_double), ("steps", ctypes.c_int64),
-                ("n_min", ctypes.c_double * 2), ("n_max", ctypes.c_double * 2)]
+                ("n_min", ctypes.c_double * 2), ("n_max", ctypes.c_double * 2),
+                ("space_charge", ctypes.c_double * 2)]
 
 
 class it_sim_desc(ctypes.Structure):
@@ -443,6 +444,7 @@ class Tallies:
     steps: int
     n_min: np.ndarray
     n_max: np.ndarray
+    space_charge: np.ndarray   # ions added per species by the space-charge term (0 when off)
 
     @property
     def collected(self):
@@ -452,19 +454,22 @@ class Tallies:
     def from_c(cls, t: it_tallies_t):
         a = lambda x: np.array([x[0], x[1]])
         return cls(a(t.released), a(t.collected_anode), a(t.collected_cathode), a(t.lost_lateral),
-                   a(t.in_domain), t.recombined, t.f, t.t_s, t.dt_s, t.steps, a(t.n_min), a(t.n_max))
+                   a(t.in_domain), t.recombined, t.f, t.t_s, t.dt_s, t.steps, a(t.n_min), a(t.n_max),
+                   a(t.space_charge))
 
 
 class Batch:
     """Many simulations advanced together (see it_batch_create)."""
 
     def __init__(self, descs, mu=(1.73, 1.87), D=(0.037, 0.037), alpha=1.6e-6, W_eV=34.0,
-                 lateral_bc=IT_PERIODIC, scheme=IT_LAX_WENDROFF, cfl_safety=1.0, react_kappa=0.5):
+                 lateral_bc=IT_PERIODIC, scheme=IT_LAX_WENDROFF, cfl_safety=1.0, react_kappa=0.5,
+                 space_charge=False):
         self.descs = [it_sim_desc(int(d["nx"]), int(d["ny"]), int(d["nz"]), float(d["dx_cm"]),
                                   float(d.get("dt_s", 0.0)), float(d["voltage_V"]), float(d.get("n_peak_cm3", 0.0)))
                       for d in descs]
         p = it_params_default(mu=mu, D=D, alpha=alpha, W_eV=W_eV, lateral_bc=lateral_bc, scheme=scheme,
-                              cfl_safety=cfl_safety, react_kappa=react_kappa, gap_cm=1.0)
+                              cfl_safety=cfl_safety, react_kappa=react_kappa, gap_cm=1.0,
+                              space_charge=int(bool(space_charge)))
         self.h = it_batch_create(self.descs, p)
 
     def deposit(self, sim, x_cm, y_cm, let_keV_um, b_cm):
@@ -524,13 +529,14 @@ class Simulation:
     def __init__(self, nx, ny, nz, dx_cm, voltage_V, dt_s=0.0, mu=(1.73, 1.87), D=(0.037, 0.037),
                  alpha=1.6e-6, W_eV=34.0, precision=IT_FP32, lateral_bc=IT_PERIODIC,
                  scheme=IT_LAX_WENDROFF, kernel=IT_KERNEL_AUTO, n_peak_cm3=0.0, cfl_safety=1.0,
-                 react_kappa=0.5, torch_state=False):
+                 react_kappa=0.5, torch_state=False, space_charge=False):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.precision = precision
         self.p = it_params_default(mu=mu, D=D, alpha=alpha, W_eV=W_eV, gap_cm=self.nz * dx_cm,
                                    voltage_V=voltage_V, precision=precision, lateral_bc=lateral_bc,
                                    scheme=scheme, kernel=kernel, n_peak_cm3=n_peak_cm3,
-                                   cfl_safety=cfl_safety, react_kappa=react_kappa)
+                                   cfl_safety=cfl_safety, react_kappa=react_kappa,
+                                   space_charge=int(bool(space_charge)))
         self._state = None
         if torch_state:
             import torch

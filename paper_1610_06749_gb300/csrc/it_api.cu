@@ -30,6 +30,9 @@ static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
 // Eq. (vNeum) with E along z and dx = dy = dz: 6 s + c^2 <= 1 (Lax-Wendroff)
 // or 6 s + c <= 1 (upwind), s = D dt/dx^2, c = mu E dt/dx.
+// elementary charge (C) over the vacuum permittivity (F/cm), V cm
+constexpr double kQOverEps0 = 1.602176634e-19 / 8.8541878128e-14;
+
 static double dt_von_neumann(const it_params *p, double dx) {
     const double E = p->voltage_V / p->gap_cm;
     double best = INFINITY;
@@ -70,6 +73,7 @@ static int check_params(const it_params *p, it_grid g, double dx) {
         return fail(IT_EINVAL, "cfl_safety must be in (0, 1]");
     if (!(std::isfinite(p->react_kappa) && p->react_kappa > 0)) return fail(IT_EINVAL, "react_kappa must be > 0");
     if (!finite_nonneg(p->n_peak_cm3)) return fail(IT_EINVAL, "n_peak must be finite and >= 0");
+    if (p->space_charge != 0 && p->space_charge != 1) return fail(IT_EINVAL, "space_charge must be 0 or 1");
     return IT_OK;
 }
 
@@ -122,6 +126,14 @@ static void make_coef(Coef<T> &cf, const it_params *p, double dx, double dt) {
     }
     cf.adt = (T)(p->alpha * dt);
     cf.rec_f = (double)cf.adt * vol;
+    // space charge, Eq. (theEquation): d n+/dt gains -mu+ n+ div E, d n-/dt gains
+    // +mu- n- div E, div E = q/eps0 (n+ - n-)
+    cf.sc_on = p->space_charge ? 1 : 0;
+    for (int s = 0; s < 2; ++s) {
+        const double sigma = s == 0 ? 1.0 : -1.0;
+        cf.sc[s] = p->space_charge ? (T)(-sigma * dt * p->mu[s] * kQOverEps0) : (T)0;
+        cf.sc_f[s] = (double)cf.sc[s] * vol;
+    }
 }
 
 static int ctx_free(it_ctx *c) {
@@ -332,6 +344,9 @@ int it_auto_dt(const it_params *p, double dx_cm, double *dt_out) {
     if (!(std::isfinite(dx_cm) && dx_cm > 0) || !(p->gap_cm > 0)) return fail(IT_EINVAL, "dx and gap must be > 0");
     double dt = p->cfl_safety * dt_von_neumann(p, dx_cm);
     if (p->alpha > 0 && p->n_peak_cm3 > 0) dt = std::min(dt, p->react_kappa / (p->alpha * p->n_peak_cm3));
+    // the space-charge term decays a lone species at the rate mu q/eps0 n
+    if (p->space_charge && p->n_peak_cm3 > 0)
+        dt = std::min(dt, p->react_kappa / (std::max(p->mu[0], p->mu[1]) * kQOverEps0 * p->n_peak_cm3));
     if (!std::isfinite(dt)) return fail(IT_EINVAL, "no finite time step (all transport constants are zero)");
     *dt_out = dt;
     return IT_OK;
@@ -563,6 +578,7 @@ int it_tallies(it_ctx *c, it_tallies_t *t) {
     t->collected_anode[0] = o[1]; t->collected_anode[1] = o[2];
     t->collected_cathode[0] = o[3]; t->collected_cathode[1] = o[4];
     t->lost_lateral[0] = o[5]; t->lost_lateral[1] = o[6];
+    t->space_charge[0] = o[7]; t->space_charge[1] = o[8];
     t->in_domain[0] = o[NT]; t->in_domain[1] = o[NT + 1];
     t->n_min[0] = o[NT + 2]; t->n_min[1] = o[NT + 3];
     t->n_max[0] = o[NT + 4]; t->n_max[1] = o[NT + 5];

@@ -39,12 +39,13 @@ struct BatchEntry {
 // per-cell operation sequence as the single-simulation kernels.  Thread t
 // owns x = t mod nx of every (256 / nx)-th row, so there is no division per
 // cell.
-template <bool PERIODIC>
+template <bool PERIODIC, bool SC>
 __global__ void __launch_bounds__(256)
 step_batched_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restrict__ tab,
                     const float *__restrict__ ip_all, const float *__restrict__ im_all, float *__restrict__ op_all,
                     float *__restrict__ om_all, double *__restrict__ slots) {
-    __shared__ double red[32 * 7];
+    constexpr int NQ = SC ? 9 : 7;   // tallies: 7, 9 with space charge
+    __shared__ double red[32 * NQ];
     __shared__ BatchSim S;
     __shared__ BatchEntry E;
     if (threadIdx.x == 0) {
@@ -59,7 +60,7 @@ step_batched_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restr
     const int plane = nx * ny;
     const int R = nx <= (int)blockDim.x ? (int)blockDim.x / nx : 1;   // rows per pass
     const int lane_row = nx <= (int)blockDim.x ? (int)threadIdx.x / nx : 0;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    double acc[NQ] = {};
     if (lane_row < R) {
         const int i0 = nx <= (int)blockDim.x ? (int)threadIdx.x - lane_row * nx : (int)threadIdx.x;
         long long row = E.begin + lane_row;
@@ -86,8 +87,12 @@ step_batched_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restr
                     const float yp = (PERIODIC || j < ny - 1) ? in[iyp] : 0.f;
                     const float zm = (k > 0) ? in[idx - plane] : 0.f;
                     const float zp = (k < nz - 1) ? in[idx + plane] : 0.f;
-                    const float v =
+                    float v =
                         upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.w0[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
+                    if constexpr (SC) {
+                        v = add_sc(v, c.sc[s], n0, p0, m0);
+                        acc[NQ - 2 + s] += (double)__fmul_rn(n0, __fsub_rn(p0, m0));
+                    }
                     (s ? om : op)[idx] = v;
                     if (k == 0) acc[1 + s] += (double)n0;
                     if (k == nz - 1) acc[3 + s] += (double)n0;
@@ -98,7 +103,7 @@ step_batched_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restr
             while (j >= ny) { j -= ny; ++k; }
         }
     }
-    block_sum<7>(acc, red);
+    block_sum<NQ>(acc, red);
     if (threadIdx.x == 0) {
         double *sl = slots + (size_t)blockIdx.x * NT;
         sl[0] += acc[0] * c.rec_f;
@@ -108,6 +113,10 @@ step_batched_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restr
         sl[4] += acc[4] * c.cathode_f[1];
         sl[5] += acc[5];
         sl[6] += acc[6];
+        if constexpr (SC) {
+            sl[7] += acc[NQ - 2] * c.sc_f[0];
+            sl[8] += acc[NQ - 1] * c.sc_f[1];
+        }
     }
 }
 
@@ -124,19 +133,22 @@ __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpre
 // registers, reads the y-neighbour rows with 16-byte loads (mostly L1/L2
 // hits: they are other threads' centres), and takes x-neighbours by warp
 // shuffle.  Same per-cell operation sequence as every other kernel.
-template <bool PERIODIC>
+template <bool PERIODIC, bool SC>
 __global__ void __launch_bounds__(256, 3)
 step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__restrict__ tab,
                         const float *__restrict__ ip_all, const float *__restrict__ im_all,
                         float *__restrict__ op_all, float *__restrict__ om_all, double *__restrict__ slots) {
-    __shared__ double wacc[8 * 8];   // per-warp FP64 tallies (tally q of warp w at w*8+q)
+    // per-warp FP64 tallies (tally q of warp w at w*WQ+q): 7 tallies, 9 with
+    // space charge; a power-of-two row keeps the index a shift
+    constexpr int WQ = SC ? 16 : 8, NQ = SC ? 9 : 7;
+    __shared__ double wacc[8 * WQ];
     __shared__ BatchSim S;
     __shared__ VecEntry E;
     if (threadIdx.x == 0) {
         E = tab[blockIdx.x];
         S = sims[E.sim];
     }
-    if (threadIdx.x < 64) wacc[threadIdx.x] = 0.0;
+    if (threadIdx.x < 8 * WQ) wacc[threadIdx.x] = 0.0;
     __syncthreads();
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     const Coef<float> &c = S.cf;
@@ -165,7 +177,7 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         double v = (double)part;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) wacc[warp * 8 + q] += v;
+        if (lane == 0) wacc[warp * WQ + q] += v;
     };
     float4 prev[2], cur[2], nxt[2];
     for (int s = 0; s < 2; ++s) {
@@ -173,7 +185,7 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         cur[s] = ldg4(in_[s] + E.z0 * plane + row);
         nxt[s] = E.z0 + 1 < nz ? ldg4(in_[s] + (E.z0 + 1) * plane + row) : zero4;
     }
-    float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f;
+    float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f, ssum0 = 0.f, ssum1 = 0.f;
     int nacc = 0;
     for (int k = E.z0; k < E.z1; ++k) {
         const int pk = k * plane;
@@ -183,6 +195,8 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         const float2 rxy = __fmul2_rn(make_float2(cur[0].x, cur[0].y), make_float2(cur[1].x, cur[1].y));
         const float2 rzw = __fmul2_rn(make_float2(cur[0].z, cur[0].w), make_float2(cur[1].z, cur[1].w));
         float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
+        float2 dxy, dzw;
+        if (SC) sc_diff4(cur[0], cur[1], dxy, dzw);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const float4 n = cur[s];
@@ -192,8 +206,13 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
             float r = __shfl_down_sync(0xffffffffu, n.x, 1);
             if (need_l) l = zero_l ? 0.f : __ldg(in_[s] + pk + row_l);
             if (need_r) r = zero_r ? 0.f : __ldg(in_[s] + pk + row_r);
-            const float4 v = upd7x4(n, l, r, u, d, prev[s], nxt[s], rxy, rzw, c.w0[s], c.wx[s], c.wy[s], c.wzm[s],
-                                    c.wzp[s], c.adt);
+            float4 v = upd7x4(n, l, r, u, d, prev[s], nxt[s], rxy, rzw, c.w0[s], c.wx[s], c.wy[s], c.wzm[s],
+                              c.wzp[s], c.adt);
+            if (SC) {
+                float2 pxy, pzw;
+                v = add_sc4(v, c.sc[s], n, dxy, dzw, pxy, pzw);
+                if (valid) (s ? ssum1 : ssum0) += (pxy.x + pxy.y) + (pzw.x + pzw.y);
+            }
             if (valid) {
                 *reinterpret_cast<float4 *>(out_[s] + pk + row) = v;
                 if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
@@ -215,6 +234,7 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
             flush(0, rsum);
             rsum = 0.f;
             if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); lsum0 = lsum1 = 0.f; }
+            if (SC) { flush(7, ssum0); flush(8, ssum1); ssum0 = ssum1 = 0.f; }
             nacc = 0;
         }
         if (k == 0) { flush(1, an[0]); flush(2, an[1]); }
@@ -222,12 +242,13 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
     }
     flush(0, rsum);
     if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); }
+    if (SC) { flush(7, ssum0); flush(8, ssum1); }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double acc[7];
-        for (int q = 0; q < 7; ++q) {
+        double acc[NQ];
+        for (int q = 0; q < NQ; ++q) {
             double v = 0.0;
-            for (int w = 0; w < 8; ++w) v += wacc[w * 8 + q];
+            for (int w = 0; w < 8; ++w) v += wacc[w * WQ + q];
             acc[q] = v;
         }
         double *sl = slots + (size_t)blockIdx.x * NT;
@@ -239,6 +260,10 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         // lateral faces: x and y weights are equal for dx = dy (latx_f == laty_f)
         sl[5] += acc[5] * c.latx_f[0];
         sl[6] += acc[6] * c.latx_f[1];
+        if (SC) {
+            sl[7] += acc[NQ - 2] * c.sc_f[0];
+            sl[8] += acc[NQ - 1] * c.sc_f[1];
+        }
     }
 }
 
@@ -469,15 +494,18 @@ int launch_batched_step(it_batch *b, int parity) {
     const float *ip = b->state[parity][0], *im = b->state[parity][1];
     float *op = b->state[parity ^ 1][0], *om = b->state[parity ^ 1][1];
     const bool per = b->p.lateral_bc == IT_PERIODIC;
+    const bool sc = b->p.space_charge != 0;
     if (nv) {
-        if (per) step_batched_vec_kernel<true><<<nv, 256, 0, b->stream>>>(b->d_sims, b->d_vtab, ip, im, op, om, b->d_slots);
-        else step_batched_vec_kernel<false><<<nv, 256, 0, b->stream>>>(b->d_sims, b->d_vtab, ip, im, op, om, b->d_slots);
+        auto *kv = per ? (sc ? step_batched_vec_kernel<true, true> : step_batched_vec_kernel<true, false>)
+                       : (sc ? step_batched_vec_kernel<false, true> : step_batched_vec_kernel<false, false>);
+        kv<<<nv, 256, 0, b->stream>>>(b->d_sims, b->d_vtab, ip, im, op, om, b->d_slots);
         IT_CK(cudaGetLastError());
     }
     if (ns) {
         double *sl = b->d_slots + (size_t)NT * nv;
-        if (per) step_batched_kernel<true><<<ns, 256, 0, b->stream>>>(b->d_sims, b->d_stab, ip, im, op, om, sl);
-        else step_batched_kernel<false><<<ns, 256, 0, b->stream>>>(b->d_sims, b->d_stab, ip, im, op, om, sl);
+        auto *ks = per ? (sc ? step_batched_kernel<true, true> : step_batched_kernel<true, false>)
+                       : (sc ? step_batched_kernel<false, true> : step_batched_kernel<false, false>);
+        ks<<<ns, 256, 0, b->stream>>>(b->d_sims, b->d_stab, ip, im, op, om, sl);
         IT_CK(cudaGetLastError());
     }
     return IT_OK;
@@ -944,6 +972,7 @@ int it_batch_tallies(it_batch *b, int32_t sim, it_tallies_t *t) {
     t->collected_anode[0] = acc[1]; t->collected_anode[1] = acc[2];
     t->collected_cathode[0] = acc[3]; t->collected_cathode[1] = acc[4];
     t->lost_lateral[0] = acc[5]; t->lost_lateral[1] = acc[6];
+    t->space_charge[0] = acc[7]; t->space_charge[1] = acc[8];
     t->released[0] = rel[0]; t->released[1] = rel[1];
     const double r = rel[0] + rel[1];
     t->f = r > 0 ? (acc[1] + acc[2] + acc[3] + acc[4]) / r : NAN;

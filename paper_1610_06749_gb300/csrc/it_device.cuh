@@ -54,4 +54,13 @@ __device__ __forceinline__ double upd7(double n, double l, double r, double u, d
     return __fma_rn(-adt, rr, v);
 }
 
+// The space-charge term of one cell, after upd7: v + sc n (n+ - n-), in this
+// operation order in every kernel (the paired form is add_sc4).
+__device__ __forceinline__ float add_sc(float v, float sc, float n, float p, float m) {
+    return __fmaf_rn(sc, __fmul_rn(n, __fsub_rn(p, m)), v);
+}
+__device__ __forceinline__ double add_sc(double v, double sc, double n, double p, double m) {
+    return __fma_rn(sc, __dmul_rn(n, __dsub_rn(p, m)), v);
+}
+
 }  // namespace itk

@@ -15,8 +15,9 @@ namespace itk {
 // Tally slots every step kernel writes per CTA (FP64, accumulated over all
 // steps by the CTA that owns the slot, so the fixed-order final reduction is
 // deterministic):
-//   0 recombined ion pairs, 1/2 anode +/-, 3/4 cathode +/-, 5/6 lateral +/-
-constexpr int NT = 8;
+//   0 recombined ion pairs, 1/2 anode +/-, 3/4 cathode +/-, 5/6 lateral +/-,
+//   7/8 ions added by the space-charge term +/- (9 unused)
+constexpr int NT = 10;
 // Monitor values of the current state per CTA: in-domain +/- (ions),
 // min +/-, max +/- (densities).
 constexpr int NM = 6;
@@ -34,11 +35,15 @@ template <typename T>
 struct Coef {
     T w0[2], wx[2], wy[2], wzm[2], wzp[2];
     T adt;            // alpha * dt
+    T sc[2];          // space charge: the update adds sc[s] n_s (n+ - n-);
+                      // sc = -dt mu+ q/eps0 for n+, +dt mu- q/eps0 for n-
+    int sc_on;        // 1: the space-charge term is on
     // FP64 factors that turn per-CTA sums into ions (weights as rounded to T)
     double rec_f;     // adt * vol
     double anode_f[2];    // wzp * vol  (cell k=0 sends wzp to the ghost k=-1)
     double cathode_f[2];  // wzm * vol  (cell k=nz-1 sends wzm to the ghost k=nz)
     double latx_f[2], laty_f[2];
+    double sc_f[2];   // sc * vol (tally of the space-charge term)
 };
 
 struct Grid {

@@ -23,10 +23,10 @@ __global__ void __launch_bounds__(256)
 step_simple_kernel(const T *__restrict__ ip, const T *__restrict__ im, T *__restrict__ op,
                    T *__restrict__ om, int nx, int ny, int nz, Coef<T> c,
                    double *__restrict__ slots) {
-    __shared__ double red[32 * 7];
+    __shared__ double red[32 * 9];
     const size_t plane = (size_t)nx * ny;
     const size_t total = plane * nz;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx % nx);
@@ -52,7 +52,11 @@ step_simple_kernel(const T *__restrict__ ip, const T *__restrict__ im, T *__rest
             const T yp = (PERIODIC || j < ny - 1) ? in[iyp] : T(0);
             const T zm = (k > 0) ? in[idx - plane] : T(0);
             const T zp = (k < nz - 1) ? in[idx + plane] : T(0);
-            const T v = upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.w0[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
+            T v = upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.w0[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
+            if (c.sc_on) {
+                v = add_sc(v, c.sc[s], n0, p0, m0);
+                acc[7 + s] += (double)(n0 * (p0 - m0));
+            }
             (s ? om : op)[idx] = v;
             if (k == 0) acc[1 + s] += (double)n0;
             if (k == nz - 1) acc[3 + s] += (double)n0;
@@ -60,7 +64,7 @@ step_simple_kernel(const T *__restrict__ ip, const T *__restrict__ im, T *__rest
                 acc[5 + s] += (double)n0 * (cx * c.latx_f[s] + cy * c.laty_f[s]);
         }
     }
-    block_sum<7>(acc, red);
+    block_sum<9>(acc, red);
     if (threadIdx.x == 0) {
         double *sl = slots + (size_t)blockIdx.x * NT;
         sl[0] += acc[0] * c.rec_f;
@@ -70,6 +74,8 @@ step_simple_kernel(const T *__restrict__ ip, const T *__restrict__ im, T *__rest
         sl[4] += acc[4] * c.cathode_f[1];
         sl[5] += acc[5];
         sl[6] += acc[6];
+        sl[7] += acc[7] * c.sc_f[0];
+        sl[8] += acc[8] * c.sc_f[1];
     }
 }
 

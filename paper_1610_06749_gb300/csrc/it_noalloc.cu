@@ -9,7 +9,7 @@
 // the step kernel needs live in a fixed array in this file's device
 // memory, so nothing is allocated.
 //
-// The array: IT_NOALLOC_MAX_BLOCKS x 8 doubles (128 KiB), held by every
+// The array: IT_NOALLOC_MAX_BLOCKS x 10 doubles (160 KiB), held by every
 // GPU that loads the library until the process exits.  Its device address
 // is looked up once per device (cudaGetSymbolAddress, with that device
 // current) on the first call made on that device; that first call should
@@ -81,6 +81,10 @@ extern "C" int it_step_noalloc(it_grid g, double dx_cm, double dt_s, const it_pa
     if (rc) return rc;
     if (p->precision != IT_FP32) {
         set_error("it_step_noalloc: FP32 densities only");
+        return IT_EINVAL;
+    }
+    if (p->space_charge) {
+        set_error("it_step_noalloc: the space-charge term is not available here (its tallies are not among the 7)");
         return IT_EINVAL;
     }
     if (!dev_plus || !dev_minus || !dev_out_plus || !dev_out_minus || !dev_tallies7) {

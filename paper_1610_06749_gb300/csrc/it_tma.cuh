@@ -164,4 +164,25 @@ __device__ __forceinline__ float4 upd7x4(float4 n, float l, float r, float4 u, f
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// The space-charge term of four cells (one float4), after upd7x4:
+// v + sc n (n+ - n-), given d = n+ - n- as pairs (formed with a paired
+// addition of -n-, which rounds like the scalar subtraction).  The same
+// operation sequence as the scalar add_sc.  pxy/pzw receive n (n+ - n-), the
+// tally of the term.
+__device__ __forceinline__ float4 add_sc4(float4 v, float sc, float4 n, float2 dxy, float2 dzw, float2 &pxy,
+                                          float2 &pzw) {
+    const float2 SC = make_float2(sc, sc);
+    pxy = __fmul2_rn(make_float2(n.x, n.y), dxy);
+    pzw = __fmul2_rn(make_float2(n.z, n.w), dzw);
+    const float2 a = __ffma2_rn(SC, pxy, make_float2(v.x, v.y));
+    const float2 b = __ffma2_rn(SC, pzw, make_float2(v.z, v.w));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// n+ - n- of four cells as pairs
+__device__ __forceinline__ void sc_diff4(float4 P, float4 M, float2 &dxy, float2 &dzw) {
+    dxy = __fadd2_rn(make_float2(P.x, P.y), make_float2(-M.x, -M.y));
+    dzw = __fadd2_rn(make_float2(P.z, P.w), make_float2(-M.z, -M.w));
+}
+
 }  // namespace itk

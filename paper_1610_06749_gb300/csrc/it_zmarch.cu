@@ -55,7 +55,7 @@ constexpr int ZM_MAX_IPT = 4;                    // float4 items per thread
 //   barrier inside the march.  The FP64 tallies live in shared memory (each
 //   warp's lane 0 adds to its own row), so the registers hold only the
 //   marching planes and offsets.
-template <bool PERIODIC, int IPT, int NW>
+template <bool PERIODIC, int IPT, int NW, bool SC>
 __global__ void __launch_bounds__(NW * 32, (NW <= 8 ? 2 : 1))
 step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp, float *__restrict__ outm,
                    int nx, int ny, int nz, const ZmConf zc, const Coef<float> cf, double *__restrict__ slots,
@@ -68,7 +68,10 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_base + (size_t)zc.S * zc.slot * sizeof(float));
     uint32_t *rel = reinterpret_cast<uint32_t *>(full + zc.S);   // release counters
     uint32_t *fills = rel + zc.S;                                  // loads issued per slot
-    __shared__ double wacc[NW * 8];      // per-warp FP64 tallies (tally q of warp w at w*8+q)
+    // per-warp FP64 tallies (tally q of warp w at w*WQ+q): 7 tallies, 9 with
+    // space charge; a power-of-two row keeps the index a shift
+    constexpr int WQ = SC ? 16 : 8, NQ = SC ? 9 : 7;
+    __shared__ double wacc[NW * WQ];
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
@@ -121,7 +124,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
             rel[q] = 0;
             fills[q] = 0;
         }
-        for (int q = 0; q < NW * 8; ++q) wacc[q] = 0.0;
+        for (int q = 0; q < NW * WQ; ++q) wacc[q] = 0.0;
         abort_flag = 0;
         fence_mbar_init();
         for (int n = 0; n < S && n < nload; ++n) issue(n);
@@ -134,7 +137,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         double v = (double)part;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) wacc[warp * 8 + q] += v;
+        if (lane == 0) wacc[warp * WQ + q] += v;
     };
 
     // per-item offsets inside a species block (species 1: + nbx*blk); x
@@ -231,7 +234,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                 cur[it][1] = *reinterpret_cast<const float4 *>(sl + sp_ofs + o_c[it]);
             }
         }
-        float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f;
+        float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f, ssum0 = 0.f, ssum1 = 0.f;
         int nacc = 0;
         // not unrolled: an unrolled march (which would save the register
         // rotation of prev/cur) measured slower
@@ -246,6 +249,8 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                 const float4 P = cur[it][0], M = cur[it][1];
                 const float2 rxy = __fmul2_rn(make_float2(P.x, P.y), make_float2(M.x, M.y));
                 const float2 rzw = __fmul2_rn(make_float2(P.z, P.w), make_float2(M.z, M.w));
+                float2 dxy, dzw;
+                if (SC) sc_diff4(P, M, dxy, dzw);
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const float *bk = sk + s * sp_ofs;
@@ -259,8 +264,13 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                         if (c4_[it] == 0) l = 0.f;
                         if (c4_[it] == ncol4 - 1) r = 0.f;
                     }
-                    const float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
-                                            cf.wzm[s], cf.wzp[s], cf.adt);
+                    float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
+                                      cf.wzm[s], cf.wzp[s], cf.adt);
+                    if (SC) {
+                        float2 pxy, pzw;
+                        v = add_sc4(v, cf.sc[s], n, dxy, dzw, pxy, pzw);
+                        if (valid[it]) (s ? ssum1 : ssum0) += (pxy.x + pxy.y) + (pzw.x + pzw.y);
+                    }
                     if (valid[it]) {
                         *reinterpret_cast<float4 *>((s ? outm : outp) + off[it]) = v;
                         if (electrode) an[s] += (n.x + n.y) + (n.z + n.w);
@@ -283,6 +293,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                 flush(0, rsum);
                 rsum = 0.f;
                 if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); lsum0 = lsum1 = 0.f; }
+                if (SC) { flush(7, ssum0); flush(8, ssum1); ssum0 = ssum1 = 0.f; }
                 nacc = 0;
             }
             if (k == 0) { flush(1, an[0]); flush(2, an[1]); }
@@ -293,6 +304,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         }
         flush(0, rsum);
         if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); }
+        if (SC) { flush(7, ssum0); flush(8, ssum1); }
         release(pc);   // the plane zb above the segment
         if (failed) break;
     }
@@ -306,10 +318,10 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
             if (fills[j] > 0) (void)mbar_wait_bounded(&full[j], (fills[j] - 1u) & 1u);
     }
     if (tid == 0 && !abort_flag) {
-        double acc[7];
-        for (int q = 0; q < 7; ++q) {
+        double acc[NQ];
+        for (int q = 0; q < NQ; ++q) {
             double t = 0.0;
-            for (int w = 0; w < NW; ++w) t += wacc[w * 8 + q];
+            for (int w = 0; w < NW; ++w) t += wacc[w * WQ + q];
             acc[q] = t;
         }
         double *sl = slots + (size_t)blockIdx.x * NT;
@@ -321,6 +333,10 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         // lateral faces: x and y weights are equal for dx = dy (latx_f == laty_f)
         sl[5] += acc[5] * cf.latx_f[0];
         sl[6] += acc[6] * cf.latx_f[1];
+        if (SC) {
+            sl[7] += acc[NQ - 2] * cf.sc_f[0];
+            sl[8] += acc[NQ - 1] * cf.sc_f[1];
+        }
     }
 }
 
@@ -370,24 +386,24 @@ static int align32f(int floats) { return (floats + 31) / 32 * 32; }   // 128-byt
 // shared by every context: raise it to the device's opt-in maximum (never
 // lower it to one context's need), so launches of other contexts with
 // larger tiles stay valid.
-template <bool P, int I, int W>
+template <bool P, int I, int W, bool S>
 static cudaError_t zm_set_attr(size_t smem) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, step_zmarch_kernel<P, I, W>);
+    e = cudaFuncGetAttributes(&fa, step_zmarch_kernel<P, I, W, S>);
     if (e != cudaSuccess) return e;
     const int max_dyn = optin - (int)fa.sharedSizeBytes;   // static shared memory counts against the limit
     if ((int)smem > max_dyn) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(step_zmarch_kernel<P, I, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+    return cudaFuncSetAttribute(step_zmarch_kernel<P, I, W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
 }
 
-template <bool P, int I, int W>
+template <bool P, int I, int W, bool S>
 static int zm_occupancy(size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_zmarch_kernel<P, I, W>, W * 32, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_zmarch_kernel<P, I, W, S>, W * 32, smem) != cudaSuccess)
         return 0;
     return n;
 }
@@ -449,12 +465,19 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid
     const int ipt = ipt_of(c, TY, nw);
     cudaError_t e = cudaSuccess;
     int occ = 0;
-#define ZM_CASE(P, I, W) \
-    if (per == P && ipt == I && nw == W) { e = zm_set_attr<P, I, W>(z.smem); occ = zm_occupancy<P, I, W>(z.smem); }
-    ZM_CASE(true, 1, 16) ZM_CASE(true, 2, 16) ZM_CASE(true, 3, 16) ZM_CASE(true, 4, 16)
-    ZM_CASE(false, 1, 16) ZM_CASE(false, 2, 16) ZM_CASE(false, 3, 16) ZM_CASE(false, 4, 16)
-    ZM_CASE(true, 1, 8) ZM_CASE(true, 2, 8) ZM_CASE(true, 3, 8) ZM_CASE(true, 4, 8)
-    ZM_CASE(false, 1, 8) ZM_CASE(false, 2, 8) ZM_CASE(false, 3, 8) ZM_CASE(false, 4, 8)
+    const bool sc = c->p.space_charge != 0;
+#define ZM_CASE(P, I, W, S)                                        \
+    if (per == P && ipt == I && nw == W && sc == S) {              \
+        e = zm_set_attr<P, I, W, S>(z.smem);                       \
+        occ = zm_occupancy<P, I, W, S>(z.smem);                    \
+    }
+#define ZM_CASES(S)                                                                          \
+    ZM_CASE(true, 1, 16, S) ZM_CASE(true, 2, 16, S) ZM_CASE(true, 3, 16, S) ZM_CASE(true, 4, 16, S) \
+    ZM_CASE(false, 1, 16, S) ZM_CASE(false, 2, 16, S) ZM_CASE(false, 3, 16, S) ZM_CASE(false, 4, 16, S) \
+    ZM_CASE(true, 1, 8, S) ZM_CASE(true, 2, 8, S) ZM_CASE(true, 3, 8, S) ZM_CASE(true, 4, 8, S) \
+    ZM_CASE(false, 1, 8, S) ZM_CASE(false, 2, 8, S) ZM_CASE(false, 3, 8, S) ZM_CASE(false, 4, 8, S)
+    ZM_CASES(false) ZM_CASES(true)
+#undef ZM_CASES
 #undef ZM_CASE
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(z-march)");
     if (occ < cps) { set_error("z-march kernel: requested CTAs per SM do not fit"); return IT_EINVAL; }
@@ -499,14 +522,18 @@ int launch_step_zmarch(it_ctx *c, cudaStream_t s) {
     const int nw = z.threads / 32;
     const int ipt = ipt_of(c, z.TY, nw);
     const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
-#define ZM_LAUNCH(P, I, W)                                                                            \
-    if (per == P && ipt == I && nw == W)                                                              \
-        step_zmarch_kernel<P, I, W><<<c->zm_grid, W * 32, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, \
-                                                                       c->d_slots, c->d_err);
-    ZM_LAUNCH(true, 1, 16) ZM_LAUNCH(true, 2, 16) ZM_LAUNCH(true, 3, 16) ZM_LAUNCH(true, 4, 16)
-    ZM_LAUNCH(false, 1, 16) ZM_LAUNCH(false, 2, 16) ZM_LAUNCH(false, 3, 16) ZM_LAUNCH(false, 4, 16)
-    ZM_LAUNCH(true, 1, 8) ZM_LAUNCH(true, 2, 8) ZM_LAUNCH(true, 3, 8) ZM_LAUNCH(true, 4, 8)
-    ZM_LAUNCH(false, 1, 8) ZM_LAUNCH(false, 2, 8) ZM_LAUNCH(false, 3, 8) ZM_LAUNCH(false, 4, 8)
+    const bool sc = c->p.space_charge != 0;
+#define ZM_LAUNCH(P, I, W, S)                                                                            \
+    if (per == P && ipt == I && nw == W && sc == S)                                                      \
+        step_zmarch_kernel<P, I, W, S><<<c->zm_grid, W * 32, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, \
+                                                                          c->d_slots, c->d_err);
+#define ZM_LAUNCHES(S)                                                                                   \
+    ZM_LAUNCH(true, 1, 16, S) ZM_LAUNCH(true, 2, 16, S) ZM_LAUNCH(true, 3, 16, S) ZM_LAUNCH(true, 4, 16, S) \
+    ZM_LAUNCH(false, 1, 16, S) ZM_LAUNCH(false, 2, 16, S) ZM_LAUNCH(false, 3, 16, S) ZM_LAUNCH(false, 4, 16, S) \
+    ZM_LAUNCH(true, 1, 8, S) ZM_LAUNCH(true, 2, 8, S) ZM_LAUNCH(true, 3, 8, S) ZM_LAUNCH(true, 4, 8, S) \
+    ZM_LAUNCH(false, 1, 8, S) ZM_LAUNCH(false, 2, 8, S) ZM_LAUNCH(false, 3, 8, S) ZM_LAUNCH(false, 4, 8, S)
+    ZM_LAUNCHES(false) ZM_LAUNCHES(true)
+#undef ZM_LAUNCHES
 #undef ZM_LAUNCH
     IT_CK(cudaGetLastError());
     c->cur = nxt;

@@ -44,7 +44,7 @@ struct Zm2Maps {
     CUtensorMap halo[2];   // two rows
 };
 
-template <bool PERIODIC, int NW>
+template <bool PERIODIC, int NW, bool SC>
 __global__ void __launch_bounds__(NW * 32, (NW <= 8 ? 2 : 1))
 step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ outp, float *__restrict__ outm, int nx,
                     int ny, int nz, const Zm2Conf zc, const Coef<float> cf, double *__restrict__ slots,
@@ -55,7 +55,10 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
     float *mid = ring + (size_t)zc.S * zc.slot;   // two intermediate planes
     uint64_t *full = reinterpret_cast<uint64_t *>(mid + 2 * (size_t)zc.mslot);
     uint32_t *fills = reinterpret_cast<uint32_t *>(full + zc.S);   // loads issued per slot
-    __shared__ double wacc[NW * 8];   // per-warp FP64 tallies (tally q of warp w at w*8+q)
+    // per-warp FP64 tallies (tally q of warp w at w*WQ+q): 7 tallies, 9 with
+    // space charge; a power-of-two row keeps the index a shift
+    constexpr int WQ = SC ? 16 : 8, NQ = SC ? 9 : 7;
+    __shared__ double wacc[NW * WQ];
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
@@ -103,7 +106,7 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
             mbar_init(&full[q], 1);
             fills[q] = 0;
         }
-        for (int q = 0; q < NW * 8; ++q) wacc[q] = 0.0;
+        for (int q = 0; q < NW * WQ; ++q) wacc[q] = 0.0;
         abort_flag = 0;
         fence_mbar_init();
         for (int n = 0; n < S && n < nload; ++n) issue(n);
@@ -114,7 +117,7 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
         double v = (double)part;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) wacc[warp * 8 + q] += v;
+        if (lane == 0) wacc[warp * WQ + q] += v;
     };
     // offset of ring row r (y = y0 - 2 + r) in a block
     auto rrow = [&](int r) {
@@ -222,7 +225,7 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
         pj = pos;
         pos.advance(S);
         Mm2[0] = Mm2[1] = Mm1[0] = Mm1[1] = zero4;
-        float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f;
+        float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f, ssum0 = 0.f, ssum1 = 0.f;
         int nacc = 0;
         for (int j = za - 1; j <= zb; ++j) {
             wait_full(pos);   // level t at plane j+1
@@ -237,6 +240,8 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
             {
                 const float2 rxy = __fmul2_rn(make_float2(Tc[0].x, Tc[0].y), make_float2(Tc[1].x, Tc[1].y));
                 const float2 rzw = __fmul2_rn(make_float2(Tc[0].z, Tc[0].w), make_float2(Tc[1].z, Tc[1].w));
+                float2 dxy, dzw;
+                if (SC) sc_diff4(Tc[0], Tc[1], dxy, dzw);
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const float *bk = sj + s * rsp;
@@ -246,8 +251,13 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
                     float l = bk[t_l], r = bk[t_r];
                     if (zero_l) l = 0.f;
                     if (zero_r) r = 0.f;
-                    const float4 v = upd7x4(Tc[s], l, r, u, d, Tp[s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
-                                            cf.wzm[s], cf.wzp[s], cf.adt);
+                    float4 v = upd7x4(Tc[s], l, r, u, d, Tp[s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
+                                      cf.wzm[s], cf.wzp[s], cf.adt);
+                    if (SC) {
+                        float2 pxy, pzw;
+                        v = add_sc4(v, cf.sc[s], Tc[s], dxy, dzw, pxy, pzw);
+                        if (own) (s ? ssum1 : ssum0) += (pxy.x + pxy.y) + (pzw.x + pzw.y);
+                    }
                     Mj[s] = jin ? v : zero4;
                     if (own) {
                         const float4 n = Tc[s];
@@ -266,6 +276,8 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
             if (has_h) {
                 const float2 rxy = __fmul2_rn(make_float2(Hc[0].x, Hc[0].y), make_float2(Hc[1].x, Hc[1].y));
                 const float2 rzw = __fmul2_rn(make_float2(Hc[0].z, Hc[0].w), make_float2(Hc[1].z, Hc[1].w));
+                float2 dxy, dzw;
+                if (SC) sc_diff4(Hc[0], Hc[1], dxy, dzw);
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const float *bk = sj + s * rsp;
@@ -275,8 +287,12 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
                     float l = bk[h_l], r = bk[h_r];
                     if (hzero_l) l = 0.f;
                     if (hzero_r) r = 0.f;
-                    const float4 v = upd7x4(Hc[s], l, r, u, d, Hp[s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
-                                            cf.wzm[s], cf.wzp[s], cf.adt);
+                    float4 v = upd7x4(Hc[s], l, r, u, d, Hp[s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
+                                      cf.wzm[s], cf.wzp[s], cf.adt);
+                    if (SC) {
+                        float2 pxy, pzw;
+                        v = add_sc4(v, cf.sc[s], Hc[s], dxy, dzw, pxy, pzw);   // halo: not tallied
+                    }
                     Hm[s] = (jin && h_in) ? v : zero4;
                     Hp[s] = Hc[s];
                     Hc[s] = zp;
@@ -302,6 +318,8 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
                 const float *mb = mid + (size_t)((j - 1) & 1) * zc.mslot;
                 const float2 rxy = __fmul2_rn(make_float2(Mm1[0].x, Mm1[0].y), make_float2(Mm1[1].x, Mm1[1].y));
                 const float2 rzw = __fmul2_rn(make_float2(Mm1[0].z, Mm1[0].w), make_float2(Mm1[1].z, Mm1[1].w));
+                float2 dxy, dzw;
+                if (SC) sc_diff4(Mm1[0], Mm1[1], dxy, dzw);
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const float *bk = mb + s * msp;
@@ -310,8 +328,13 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
                     float l = bk[m_l], r = bk[m_r];
                     if (zero_l) l = 0.f;
                     if (zero_r) r = 0.f;
-                    const float4 v = upd7x4(Mm1[s], l, r, u, d, Mm2[s], Mj[s], rxy, rzw, cf.w0[s], cf.wx[s],
-                                            cf.wy[s], cf.wzm[s], cf.wzp[s], cf.adt);
+                    float4 v = upd7x4(Mm1[s], l, r, u, d, Mm2[s], Mj[s], rxy, rzw, cf.w0[s], cf.wx[s],
+                                      cf.wy[s], cf.wzm[s], cf.wzp[s], cf.adt);
+                    if (SC) {
+                        float2 pxy, pzw;
+                        v = add_sc4(v, cf.sc[s], Mm1[s], dxy, dzw, pxy, pzw);
+                        (s ? ssum1 : ssum0) += (pxy.x + pxy.y) + (pzw.x + pzw.y);
+                    }
                     *reinterpret_cast<float4 *>((s ? outm : outp) + off) = v;
                     const float4 n = Mm1[s];
                     if (j - 1 == 0 || j - 1 == nz - 1) an2[s] += (n.x + n.y) + (n.z + n.w);
@@ -332,6 +355,7 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
                 flush(0, rsum);
                 rsum = 0.f;
                 if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); lsum0 = lsum1 = 0.f; }
+                if (SC) { flush(7, ssum0); flush(8, ssum1); ssum0 = ssum1 = 0.f; }
                 nacc = 0;
             }
             // anode: plane 0, cathode: plane nz-1, of either step
@@ -344,6 +368,7 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
         }
         flush(0, rsum);
         if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); }
+        if (SC) { flush(7, ssum0); flush(8, ssum1); }
         seq0 += zb - za + 4;
         // hand back plane zb+1 too: the next segment waits for its first three
         // planes before its first barrier, and with S = 3 one of them goes
@@ -360,10 +385,10 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
             if (fills[q] > 0) (void)mbar_wait_bounded(&full[q], (fills[q] - 1u) & 1u);
     }
     if (tid == 0 && !abort_flag) {
-        double acc[7];
-        for (int q = 0; q < 7; ++q) {
+        double acc[NQ];
+        for (int q = 0; q < NQ; ++q) {
             double t = 0.0;
-            for (int w = 0; w < NW; ++w) t += wacc[w * 8 + q];
+            for (int w = 0; w < NW; ++w) t += wacc[w * WQ + q];
             acc[q] = t;
         }
         double *sl = slots + (size_t)blockIdx.x * NT;
@@ -374,6 +399,10 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
         sl[4] += acc[4] * cf.cathode_f[1];
         sl[5] += acc[5] * cf.latx_f[0];
         sl[6] += acc[6] * cf.latx_f[1];
+        if (SC) {
+            sl[7] += acc[NQ - 2] * cf.sc_f[0];
+            sl[8] += acc[NQ - 1] * cf.sc_f[1];
+        }
     }
 }
 
@@ -382,20 +411,20 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
 // ---------------------------------------------------------------------------
 static int align32f2(int floats) { return (floats + 31) / 32 * 32; }
 
-template <bool P, int W>
+template <bool P, int W, bool S>
 static cudaError_t zm2_set_attr(size_t smem, int *occ) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, step_zmarch2_kernel<P, W>);
+    e = cudaFuncGetAttributes(&fa, step_zmarch2_kernel<P, W, S>);
     if (e != cudaSuccess) return e;
     const int max_dyn = optin - (int)fa.sharedSizeBytes;   // static shared memory counts against the limit
     if ((int)smem > max_dyn) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(step_zmarch2_kernel<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+    e = cudaFuncSetAttribute(step_zmarch2_kernel<P, W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step_zmarch2_kernel<P, W>, W * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step_zmarch2_kernel<P, W, S>, W * 32, smem);
 }
 
 // Fill c->zm2 for a tile height / CTAs per SM / ring depth / grid rule (0 =
@@ -455,10 +484,11 @@ int zmarch2_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_gri
     const bool per = c->p.lateral_bc == IT_PERIODIC;
     cudaError_t e = cudaSuccess;
     int occ = 0;
-    if (per && nw == 16) e = zm2_set_attr<true, 16>(z.smem, &occ);
-    if (per && nw == 8) e = zm2_set_attr<true, 8>(z.smem, &occ);
-    if (!per && nw == 16) e = zm2_set_attr<false, 16>(z.smem, &occ);
-    if (!per && nw == 8) e = zm2_set_attr<false, 8>(z.smem, &occ);
+    const bool sc = c->p.space_charge != 0;
+    if (per && nw == 16) e = sc ? zm2_set_attr<true, 16, true>(z.smem, &occ) : zm2_set_attr<true, 16, false>(z.smem, &occ);
+    if (per && nw == 8) e = sc ? zm2_set_attr<true, 8, true>(z.smem, &occ) : zm2_set_attr<true, 8, false>(z.smem, &occ);
+    if (!per && nw == 16) e = sc ? zm2_set_attr<false, 16, true>(z.smem, &occ) : zm2_set_attr<false, 16, false>(z.smem, &occ);
+    if (!per && nw == 8) e = sc ? zm2_set_attr<false, 8, true>(z.smem, &occ) : zm2_set_attr<false, 8, false>(z.smem, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(two-step z-march)");
     if (occ < cps) { set_error("two-step z-march kernel: requested CTAs per SM do not fit"); return IT_EINVAL; }
     z.ctas_per_sm = cps;
@@ -496,14 +526,14 @@ int launch_step_zmarch2(it_ctx *c, cudaStream_t s) {
     const bool per = c->p.lateral_bc == IT_PERIODIC;
     const int nw = z.threads / 32;
     const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
-    if (per && nw == 16)
-        step_zmarch2_kernel<true, 16><<<z.grid, 512, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, c->d_slots, c->d_err);
-    if (per && nw == 8)
-        step_zmarch2_kernel<true, 8><<<z.grid, 256, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, c->d_slots, c->d_err);
-    if (!per && nw == 16)
-        step_zmarch2_kernel<false, 16><<<z.grid, 512, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, c->d_slots, c->d_err);
-    if (!per && nw == 8)
-        step_zmarch2_kernel<false, 8><<<z.grid, 256, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, c->d_slots, c->d_err);
+    const bool sc = c->p.space_charge != 0;
+#define ZM2_LAUNCH(P, W, S)                                                                              \
+    if (per == P && nw == W && sc == S)                                                                  \
+        step_zmarch2_kernel<P, W, S><<<z.grid, W * 32, z.smem, s>>>(maps, op, om, nx, ny, nz, z, c->cf, c->d_slots, \
+                                                                   c->d_err);
+    ZM2_LAUNCH(true, 16, false) ZM2_LAUNCH(true, 8, false) ZM2_LAUNCH(false, 16, false) ZM2_LAUNCH(false, 8, false)
+    ZM2_LAUNCH(true, 16, true) ZM2_LAUNCH(true, 8, true) ZM2_LAUNCH(false, 16, true) ZM2_LAUNCH(false, 8, true)
+#undef ZM2_LAUNCH
     IT_CK(cudaGetLastError());
     c->cur = nxt;
     return IT_OK;

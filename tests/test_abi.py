@@ -1,9 +1,12 @@
 """The C-ABI library builds, loads and exports what include/iontracks.h
 declares; host-only entry points work without a GPU and agree with the
 oracle's time-step rule; device entry points fail loudly without a GPU."""
+import ctypes
 import math
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -65,6 +68,62 @@ def test_auto_dt_matches_oracle_rule(L, scheme, dx, V, d):
         assert got == pytest.approx(want, rel=1e-14)
 
 
+@pytest.mark.parametrize("n_peak", [1e12, 1e13, 9.4e13])
+def test_auto_dt_with_space_charge_matches_oracle_rule(L, n_peak):
+    """With the space-charge term on, the automatic dt also keeps
+    max mu q/eps0 n_peak dt <= kappa, exactly as the oracle's rule."""
+    for dx, V, d in [(5e-4, 200.0, 0.2), (2e-4, 50.0, 0.02)]:
+        p = B.it_params_default(gap_cm=d, voltage_V=V, n_peak_cm3=n_peak, space_charge=1)
+        want = o.dt_rule(dx, V, d, (1.73, 1.87), (0.037, 0.037), 1.6e-6, n_peak=n_peak, space_charge=True)
+        assert B.it_auto_dt(p, dx) == pytest.approx(want, rel=1e-14)
+        off = B.it_auto_dt(B.it_params_default(gap_cm=d, voltage_V=V, n_peak_cm3=n_peak), dx)
+        assert B.it_auto_dt(p, dx) <= off
+
+
+_LAYOUT_C = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "iontracks.h"
+#define F(T, f) printf(#T " " #f " %zu\n", offsetof(T, f));
+#define S(T) printf(#T " sizeof %zu\n", sizeof(T));
+int main(void) {
+    S(it_params) F(it_params, mu) F(it_params, D) F(it_params, alpha) F(it_params, W_eV)
+    F(it_params, gap_cm) F(it_params, voltage_V) F(it_params, precision) F(it_params, lateral_bc)
+    F(it_params, scheme) F(it_params, kernel) F(it_params, cfl_safety) F(it_params, react_kappa)
+    F(it_params, n_peak_cm3) F(it_params, space_charge) F(it_params, reserved)
+    S(it_tallies_t) F(it_tallies_t, released) F(it_tallies_t, collected_anode)
+    F(it_tallies_t, collected_cathode) F(it_tallies_t, lost_lateral) F(it_tallies_t, in_domain)
+    F(it_tallies_t, recombined) F(it_tallies_t, f) F(it_tallies_t, t_s) F(it_tallies_t, dt_s)
+    F(it_tallies_t, steps) F(it_tallies_t, n_min) F(it_tallies_t, n_max) F(it_tallies_t, space_charge)
+    S(it_sim_desc) F(it_sim_desc, nx) F(it_sim_desc, ny) F(it_sim_desc, nz) F(it_sim_desc, dx_cm)
+    F(it_sim_desc, dt_s) F(it_sim_desc, voltage_V) F(it_sim_desc, n_peak_cm3)
+    S(it_grid)
+    return 0;
+}
+"""
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes struct has the size and field offsets the C compiler
+    gives the header's struct."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        tname, field, val = line.split()
+        cls = getattr(B, tname)
+        got = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert got == int(val), (tname, field, got, val)
+        seen += 1
+    assert seen == 39
+
+
 def test_peak_density_and_state_bytes(L):
     let, b = np.array([1.0, 1000.0, 10.0]), np.array([1e-3, 1e-3, 5e-4])
     assert B.it_peak_density(let, b) == pytest.approx(o.peak_track_density(let, b), rel=1e-15)
@@ -85,6 +144,10 @@ def test_invalid_parameters_are_rejected(L):
     p3 = B.it_params_default(gap_cm=0.02, voltage_V=float("nan"))
     with pytest.raises(B.ItError) as e:
         B.it_create(48, 48, 100, 2e-4, 0.0, p3)
+    assert e.value.code == B.IT_EINVAL
+    p4 = B.it_params_default(gap_cm=0.02, voltage_V=200.0, space_charge=2)
+    with pytest.raises(B.ItError) as e:
+        B.it_create(48, 48, 100, 2e-4, 0.0, p4)
     assert e.value.code == B.IT_EINVAL
     # dt above the von Neumann bound
     dt = B.it_auto_dt(p, 2e-4)
