@@ -64,6 +64,7 @@ typedef struct {
     int space_charge;     /* 1: include the -/+ mu n div E term */
     double sc_added[2];   /* ions added to each species by that term (negative: removed) */
     int64_t steps;
+    double t;             /* simulated time: the sum of the steps' dt */
 } orc_state;
 
 /* Elementary charge (C) and vacuum permittivity (F/cm): div E = Q/EPS0 (n+ - n-)
@@ -259,7 +260,19 @@ void orc_step(orc_state *S) {
         double *t = S->n[s]; S->n[s] = S->nn[s]; S->nn[s] = t;
     }
     S->steps += 1;
+    S->t += S->dt;
 }
+
+/* Change the time step for the steps that follow (the step-size ladder of a
+ * run to completion).  Returns 0, or -1 for a dt that is not positive. */
+int orc_set_dt(orc_state *S, double dt) {
+    if (!(dt > 0)) return -1;
+    S->dt = dt;
+    return 0;
+}
+
+/* Simulated time so far: the sum of the dt of every step taken. */
+double orc_time(const orc_state *S) { return S->t; }
 
 void orc_steps(orc_state *S, int64_t n) { for (int64_t l = 0; l < n; ++l) orc_step(S); }
 

@@ -15,6 +15,10 @@ Contents
   kappa / (alpha n_peak); the paper states no bound for the reaction term, so
   this is a reading (explicit Euler on dn/dt = -alpha n^2 is stable only for
   alpha dt n < 2; kappa = 0.5 keeps it monotone).
+* ``ladder_dt`` and ``Oracle.run_to_completion(ladder=True)`` -- the same
+  bound applied at every completion check to the state's current peak density,
+  raising dt by powers of two up to the Eq. (vNeum) step (a reading: the
+  densest cells, which set the initial bound, recombine first).
 * Closed forms used as pins: ``ei`` (exponential integral of the Jaffe
   section, own series/asymptotic code), ``jaffe_parallel`` (Eq. Jaffe_noangle),
   ``jaffe_angle`` (Eq. angle), ``boag_2vm`` (the p = 0 limit of the Boag
@@ -65,6 +69,10 @@ def _load():
         lib.orc_set_density.argtypes = [p, dp, dp]
         lib.orc_set_space_charge.argtypes = [p, i]
         lib.orc_space_charge.argtypes = [p, dp]
+        lib.orc_set_dt.argtypes = [p, d]
+        lib.orc_set_dt.restype = ctypes.c_int
+        lib.orc_time.argtypes = [p]
+        lib.orc_time.restype = d
         _lib = lib
     return _lib
 
@@ -85,6 +93,8 @@ class Tallies:
     n_min: np.ndarray
     n_max: np.ndarray
     space_charge: np.ndarray = None   # [2] ions added by the space-charge term (negative: removed)
+    t_s: float = 0.0                  # simulated time, the sum of every step's dt
+    dt_s: float = 0.0                 # the current time step
 
     @property
     def collected(self) -> np.ndarray:
@@ -110,6 +120,8 @@ class Oracle:
         self.gap = self.nz * self.dx
         self.E = float(voltage_V) / self.gap
         self.W = float(W_eV)
+        self.V, self.mu, self.D = float(voltage_V), (float(mu[0]), float(mu[1])), (float(D[0]), float(D[1]))
+        self.alpha, self.scheme, self.space_charge = float(alpha), int(scheme), bool(space_charge)
         self._h = lib.orc_create(self.nx, self.ny, self.nz, self.dx, self.dt,
                                  float(mu[0]), float(mu[1]), float(D[0]), float(D[1]),
                                  float(alpha), self.E, int(lateral_bc), int(scheme))
@@ -142,6 +154,44 @@ class Oracle:
 
     def step(self, n: int = 1):
         _load().orc_steps(self._h, int(n))
+
+    def set_dt(self, dt_s: float):
+        """Time step of the steps that follow."""
+        if _load().orc_set_dt(self._h, float(dt_s)) != 0:
+            raise ValueError("oracle: dt must be positive")
+        self.dt = float(dt_s)
+
+    def run_to_completion(self, tol=1e-6, max_steps=10_000_000, check_every=64, ladder=False, kappa=0.5,
+                          cfl_safety=1.0):
+        """Step until the tracks are dragged apart (Sec. Implementation,
+        P:246): at every check (the first before any step, then every
+        check_every steps) stop when the ions left in the domain are below
+        tol of the released ones (or nothing was released).  With
+        ladder=True each check first raises dt by ladder_dt from the state's
+        peak density, capped at cfl_safety times the Eq. (vNeum) step.
+
+        Returns (steps taken, completed, log) where log lists
+        (step, dt, n_max) for the initial dt and every change."""
+        start = self.tallies().steps
+        log = [(start, self.dt, float("nan"))]
+        cap = cfl_safety * dt_von_neumann(self.dx, self.V, self.gap, self.mu, self.D, self.scheme)
+        while True:
+            t = self.tallies()
+            rel = float(t.released.sum())
+            if rel > 0 and float(t.in_domain.sum()) / rel < tol:
+                return t.steps - start, True, log
+            if rel == 0:
+                return t.steps - start, True, log
+            left = start + max_steps - t.steps
+            if left <= 0:
+                return t.steps - start, False, log
+            if ladder:
+                nmax = float(max(t.n_max[0], t.n_max[1]))
+                nd = ladder_dt(self.dt, nmax, self.alpha, cap, kappa, max(self.mu), self.space_charge)
+                if nd > self.dt:
+                    self.set_dt(nd)
+                    log.append((t.steps, nd, nmax))
+            self.step(min(check_every, left))
 
     def run_schedule(self, x_cm, y_cm, let, b, step_idx, n_steps: int, start_step: int = 0):
         """Deposit each track at the start of its arrival step, then step."""
@@ -197,7 +247,8 @@ class Oracle:
         return Tallies(released=t[0:2].copy(), collected_anode=t[2:4].copy(),
                        collected_cathode=t[4:6].copy(), lost_lateral=t[6:8].copy(),
                        in_domain=ind, recombined=float(t[8]), steps=int(t[9]),
-                       n_min=mm[[0, 2]].copy(), n_max=mm[[1, 3]].copy(), space_charge=sc)
+                       n_min=mm[[0, 2]].copy(), n_max=mm[[1, 3]].copy(), space_charge=sc,
+                       t_s=float(lib.orc_time(self._h)), dt_s=self.dt)
 
     def density(self, species: int) -> np.ndarray:
         out = np.empty((self.nz, self.ny, self.nx), dtype=np.float64)
@@ -267,6 +318,28 @@ def dt_rule(dx_cm, voltage_V, gap_cm, mu=(1.73, 1.87), D=(0.037, 0.037), alpha=1
     if space_charge and n_peak > 0:
         dt = min(dt, kappa / (max(mu) * Q_OVER_EPS0 * n_peak))
     return dt
+
+
+def ladder_dt(dt, n_max, alpha, dt_cap, kappa=0.5, mu_max=0.0, space_charge=False, max_doublings=60) -> float:
+    """One check of the doubling step-size ladder (reading: the paper's dt
+    rule, Eq. vNeum, covers transport only; the reaction bound of dt_rule is
+    set by the densest cells, which recombine first).  Returns
+    min(dt_cap, dt 2^j) for the largest j >= 0 with alpha (dt 2^j) n_max <=
+    kappa, and with the space-charge term also mu_max q/eps0 (dt 2^j) n_max
+    <= kappa; never less than dt (the ladder only rises).  Products are
+    formed left to right."""
+    def within(r):
+        if alpha * r * n_max > kappa:
+            return False
+        if space_charge and mu_max * Q_OVER_EPS0 * r * n_max > kappa:
+            return False
+        return True
+    r = dt
+    for _ in range(max_doublings):
+        if not (r < dt_cap and within(2.0 * r)):
+            break
+        r *= 2.0
+    return max(dt, min(r, dt_cap))
 
 
 # ---------------------------------------------------------------------------
