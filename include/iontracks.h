@@ -97,7 +97,8 @@ typedef struct {
                                -/+ mu n div E with div E = q/eps0 (n+ - n-) (Maxwell-Gauss),
                                from the old level; the automatic dt then also satisfies
                                dt <= react_kappa / (max mu q/eps0 n_peak).  Default 0 */
-    int32_t reserved;       /* 0 */
+    int32_t dt_ladder;      /* 1: it_run_to_completion raises dt at each check by the
+                               doubling ladder (see there); 0: dt stays fixed.  Default 0 */
 } it_params;
 
 typedef struct {
@@ -108,7 +109,7 @@ typedef struct {
     double in_domain[2];         /* ions still in the domain */
     double recombined;           /* ion pairs recombined */
     double f;                    /* (collected+ + collected-) / (released+ + released-) */
-    double t_s;                  /* simulated time */
+    double t_s;                  /* simulated time: the sum of every step's dt */
     double dt_s;                 /* time step */
     int64_t steps;               /* steps taken */
     double n_min[2], n_max[2];   /* extreme densities of the current state */
@@ -196,7 +197,18 @@ int it_step(it_ctx *ctx, int64_t n_steps);
  * ("dragged completely apart", Sec. Implementation), checked every
  * check_every steps, or until max_steps more steps.  *steps_done (may be NULL)
  * receives the steps taken.  Returns IT_EUNSTABLE if the state went
- * non-finite, IT_ETIMEOUT if max_steps ran out first. */
+ * non-finite, IT_ETIMEOUT if max_steps ran out first.
+ *
+ * With params.dt_ladder = 1 and no scheduled tracks still to come, each check
+ * that does not end the run first raises dt to min(cap, dt 2^j), j >= 0 the
+ * largest integer with alpha (dt 2^j) n_max <= react_kappa (with the
+ * space-charge term also max(mu) q/eps0 (dt 2^j) n_max <= react_kappa), where
+ * n_max is the larger species maximum of the current state and cap is
+ * cfl_safety times the Eq. (vNeum) step.  The recombination bound of
+ * it_auto_dt is set by the densest cells, which recombine first; the ladder
+ * applies the same bound to the state as it thins out, and never lowers dt.
+ * Each change is logged (it_dt_log); the weights are rebuilt and the graph
+ * segment recaptured. */
 int it_run_to_completion(it_ctx *ctx, double tol, int64_t max_steps,
                          int64_t check_every, int64_t *steps_done);
 
@@ -229,18 +241,29 @@ int it_get_density(it_ctx *ctx, int species, void *host_dst, size_t bytes);
 
 /* Replace both species' densities with host arrays (context precision,
  * [nz][ny][nx]) as an initial condition: all tallies restart, released
- * becomes the FP64 sum of what was set, the step counter returns to 0. */
+ * becomes the FP64 sum of what was set, the step counter and time return to
+ * 0 and the time-step log restarts. */
 int it_set_density(it_ctx *ctx, const void *plus, const void *minus, size_t bytes);
 
 /* Set the time step before the first step (IT_ESTATE otherwise).  dt_s > 0
  * is checked against Eq. (vNeum); dt_s <= 0 applies it_auto_dt with n_peak
  * taken as the largest density of the current state (the deposited pulse,
  * overlaps of tracks included).  The recombination bound then holds for the
- * state actually deposited. */
+ * state actually deposited.  The time-step log restarts from the new dt. */
 int it_retime(it_ctx *ctx, double dt_s);
 
+/* The time-step log: entry q holds the first step run with a dt
+ * (first_step[q]), that dt (dt[q], s) and the peak density that decided it
+ * (n_max[q], ions/cm^3; NaN for a dt set at creation, it_retime, it_reset or
+ * it_set_density).  Entry 0 is the dt in force at step 0; it_run_to_completion
+ * with the ladder appends one entry per rise.  Up to cap entries are written
+ * to the caller's arrays (which may be NULL when cap is 0); *count receives
+ * the number of entries in the log. */
+int it_dt_log(it_ctx *ctx, int64_t cap, int64_t *first_step, double *dt, double *n_max, int64_t *count);
+
 /* Return the context to its freshly created state without reallocating:
- * densities zero, all tallies zero, step counter 0, schedule cleared.
+ * densities zero, all tallies zero, step counter and time 0, schedule
+ * cleared; the current dt stays and the time-step log restarts from it.
  * Asynchronous on the context stream (no host synchronisation). */
 int it_reset(it_ctx *ctx);
 
@@ -337,7 +360,11 @@ int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us);
 
 /* Run every simulation until its in-domain charge / released < tol or it
  * has taken max_steps steps, checked every check_every steps (rounded up to
- * even).  *launches (may be NULL) receives the number of step launches. */
+ * even).  *launches (may be NULL) receives the number of step launches.
+ * With common->dt_ladder = 1 every check also applies the doubling ladder of
+ * it_run_to_completion to each active simulation whose pulses have all been
+ * deposited (its own dx, voltage and peak density), so a simulation run in
+ * the batch takes the same time steps as in its own context. */
 int it_batch_run(it_batch *b, double tol, int64_t max_steps, int64_t check_every, int64_t *launches);
 
 /* Tallies of one simulation (FP64; as it_tallies). */

@@ -42,7 +42,7 @@ class it_params(ctypes.Structure):
                 ("W_eV", ctypes.c_double), ("gap_cm", ctypes.c_double), ("voltage_V", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("lateral_bc", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("cfl_safety", ctypes.c_double), ("react_kappa", ctypes.c_double),
-                ("n_peak_cm3", ctypes.c_double), ("space_charge", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_peak_cm3", ctypes.c_double), ("space_charge", ctypes.c_int32), ("dt_ladder", ctypes.c_int32)]
 
 
 class it_tallies_t(ctypes.Structure):
@@ -95,6 +95,7 @@ def lib():
             "it_set_density": (I, [P, P, P, SZ]),
             "it_reset": (I, [P]),
             "it_retime": (I, [P, D]),
+            "it_dt_log": (I, [P, I64, I64P, DP, DP, I64P]),
             "it_batch_retime": (I, [P]),
             "it_device_state": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),
             "it_set_launch": (I, [P, I, I, I, I]),
@@ -265,6 +266,18 @@ def it_batch_retime(h):
 
 def it_reset(h):
     _check(lib().it_reset(h))
+
+
+def it_dt_log(h):
+    """The time-step log: a list of (first step, dt, deciding n_max)."""
+    n = ctypes.c_int64()
+    _check(lib().it_dt_log(h, 0, None, None, None, ctypes.byref(n)))
+    m = n.value
+    st = (ctypes.c_int64 * m)()
+    dt = (ctypes.c_double * m)()
+    nm = (ctypes.c_double * m)()
+    _check(lib().it_dt_log(h, m, st, dt, nm, ctypes.byref(n)))
+    return [(int(st[q]), float(dt[q]), float(nm[q])) for q in range(m)]
 
 
 def it_device_state(h):
@@ -463,13 +476,13 @@ class Batch:
 
     def __init__(self, descs, mu=(1.73, 1.87), D=(0.037, 0.037), alpha=1.6e-6, W_eV=34.0,
                  lateral_bc=IT_PERIODIC, scheme=IT_LAX_WENDROFF, cfl_safety=1.0, react_kappa=0.5,
-                 space_charge=False):
+                 space_charge=False, dt_ladder=False):
         self.descs = [it_sim_desc(int(d["nx"]), int(d["ny"]), int(d["nz"]), float(d["dx_cm"]),
                                   float(d.get("dt_s", 0.0)), float(d["voltage_V"]), float(d.get("n_peak_cm3", 0.0)))
                       for d in descs]
         p = it_params_default(mu=mu, D=D, alpha=alpha, W_eV=W_eV, lateral_bc=lateral_bc, scheme=scheme,
                               cfl_safety=cfl_safety, react_kappa=react_kappa, gap_cm=1.0,
-                              space_charge=int(bool(space_charge)))
+                              space_charge=int(bool(space_charge)), dt_ladder=int(bool(dt_ladder)))
         self.h = it_batch_create(self.descs, p)
 
     def deposit(self, sim, x_cm, y_cm, let_keV_um, b_cm):
@@ -529,14 +542,14 @@ class Simulation:
     def __init__(self, nx, ny, nz, dx_cm, voltage_V, dt_s=0.0, mu=(1.73, 1.87), D=(0.037, 0.037),
                  alpha=1.6e-6, W_eV=34.0, precision=IT_FP32, lateral_bc=IT_PERIODIC,
                  scheme=IT_LAX_WENDROFF, kernel=IT_KERNEL_AUTO, n_peak_cm3=0.0, cfl_safety=1.0,
-                 react_kappa=0.5, torch_state=False, space_charge=False):
+                 react_kappa=0.5, torch_state=False, space_charge=False, dt_ladder=False):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.precision = precision
         self.p = it_params_default(mu=mu, D=D, alpha=alpha, W_eV=W_eV, gap_cm=self.nz * dx_cm,
                                    voltage_V=voltage_V, precision=precision, lateral_bc=lateral_bc,
                                    scheme=scheme, kernel=kernel, n_peak_cm3=n_peak_cm3,
                                    cfl_safety=cfl_safety, react_kappa=react_kappa,
-                                   space_charge=int(bool(space_charge)))
+                                   space_charge=int(bool(space_charge)), dt_ladder=int(bool(dt_ladder)))
         self._state = None
         if torch_state:
             import torch
@@ -588,6 +601,10 @@ class Simulation:
         """Before the first step: dt_s > 0 sets it; 0 derives it from the
         largest density of the current (deposited) state."""
         it_retime(self.h, dt_s)
+
+    def dt_log(self):
+        """[(first step, dt, deciding n_max)] of every time step used."""
+        return it_dt_log(self.h)
 
     def launch(self):
         return it_get_launch(self.h)

@@ -74,6 +74,7 @@ static int check_params(const it_params *p, it_grid g, double dx) {
     if (!(std::isfinite(p->react_kappa) && p->react_kappa > 0)) return fail(IT_EINVAL, "react_kappa must be > 0");
     if (!finite_nonneg(p->n_peak_cm3)) return fail(IT_EINVAL, "n_peak must be finite and >= 0");
     if (p->space_charge != 0 && p->space_charge != 1) return fail(IT_EINVAL, "space_charge must be 0 or 1");
+    if (p->dt_ladder != 0 && p->dt_ladder != 1) return fail(IT_EINVAL, "dt_ladder must be 0 or 1");
     return IT_OK;
 }
 
@@ -251,18 +252,50 @@ static int run_plain(it_ctx *c, int64_t n) {
         IT_CK(cudaGraphLaunch(c->graph, c->stream));
         n -= kGraphSteps;
         c->steps += kGraphSteps;
+        c->t_s += c->dt * kGraphSteps;
     }
     for (; n >= 2; n -= 2) {
         int rc = two_steps(c);
         if (rc) return rc;
         c->steps += 2;
+        c->t_s += c->dt * 2;
     }
     if (n == 1) {
         int rc = one_step(c);
         if (rc) return rc;
         c->steps += 1;
+        c->t_s += c->dt;
     }
     return IT_OK;
+}
+
+// New time step for the steps that follow: weights, the log, and a new graph
+// (a captured segment holds the old weights).
+static void set_dt(it_ctx *c, double dt, double nmax) {
+    c->dt = dt;
+    make_coef(c->cf, &c->p, c->dx, dt);
+    make_coef(c->cd, &c->p, c->dx, dt);
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    c->log_step.push_back(c->steps);
+    c->log_dt.push_back(dt);
+    c->log_nmax.push_back(nmax);
+}
+
+// One check of the doubling ladder: min(cap, dt 2^j) for the largest j >= 0
+// with alpha (dt 2^j) n_max <= kappa (and, with space charge,
+// max mu q/eps0 (dt 2^j) n_max <= kappa), never below dt.  cap is
+// cfl_safety times the Eq. (vNeum) step.  Products are formed left to right.
+double ladder_rung(const it_params *p, double dx, double dt, double nmax) {
+    const double cap = p->cfl_safety * dt_von_neumann(p, dx);
+    const double mu_max = std::max(p->mu[0], p->mu[1]);
+    auto within = [&](double r) {
+        if (p->alpha * r * nmax > p->react_kappa) return false;
+        if (p->space_charge && mu_max * kQOverEps0 * r * nmax > p->react_kappa) return false;
+        return true;
+    };
+    double r = dt;
+    for (int q = 0; q < 60 && r < cap && within(2.0 * r); ++q) r *= 2.0;
+    return std::max(dt, std::min(r, cap));
 }
 
 // Parameter and time-step checks of it_create, for entry points that take
@@ -403,6 +436,9 @@ int it_create_ex(it_grid g, double dx_cm, double dt_s, const it_params *p, void 
     c->prec = p->precision;
     c->esize = p->precision == IT_FP64 ? 8 : 4;
     c->graph_parity = -1;
+    c->log_step.assign(1, 0);
+    c->log_dt.assign(1, dt);
+    c->log_nmax.assign(1, std::nan(""));
 
     auto bail = [&](int code) { ctx_free(c); return code; };
 
@@ -588,7 +624,7 @@ int it_tallies(it_ctx *c, it_tallies_t *t) {
     t->f = rel > 0 ? col / rel : NAN;
     t->steps = c->steps;
     t->dt_s = c->dt;
-    t->t_s = c->dt * (double)c->steps;
+    t->t_s = c->t_s;
     if (o[NT + NM + 2] != 0.0) return fail(IT_ETIMEOUT, "a bounded device wait ran out in the step kernel");
     return IT_OK;
 }
@@ -610,6 +646,12 @@ int it_run_to_completion(it_ctx *c, double tol, int64_t max_steps, int64_t check
         if (!pending && rel == 0) break;
         const int64_t left = start + max_steps - c->steps;
         if (left <= 0) { rc = fail(IT_ETIMEOUT, "max_steps reached before completion"); break; }
+        // the ladder: only while no scheduled deposit can raise the densities
+        if (c->p.dt_ladder && !pending) {
+            const double nmax = std::max(t.n_max[0], t.n_max[1]);
+            const double nd = ladder_rung(&c->p, c->dx, c->dt, nmax);
+            if (nd > c->dt) set_dt(c, nd, nmax);
+        }
         rc = it_step(c, std::min(check_every, left));
         if (rc) break;
     }
@@ -672,7 +714,11 @@ int it_set_density(it_ctx *c, const void *plus, const void *minus, size_t bytes)
     IT_CK(cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream));
     IT_CK(cudaMemsetAsync(c->d_acc, 0, sizeof(DevAcc), c->stream));
     c->steps = 0;
+    c->t_s = 0.0;
     c->sched_step.clear(); c->sched_tr.clear(); c->sched_ptr = 0;
+    c->log_step.assign(1, 0);
+    c->log_dt.assign(1, c->dt);
+    c->log_nmax.assign(1, std::nan(""));
     it_tallies_t t;
     int rc = it_tallies(c, &t);
     if (rc) return rc;
@@ -702,10 +748,8 @@ int it_retime(it_ctx *c, double dt_s) {
         return fail(IT_EINVAL, "dt exceeds the von Neumann bound of Eq. (vNeum)");
     }
     c->p = p;
-    c->dt = dt;
-    make_coef(c->cf, &c->p, c->dx, dt);
-    make_coef(c->cd, &c->p, c->dx, dt);
-    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    c->log_step.clear(); c->log_dt.clear(); c->log_nmax.clear();
+    set_dt(c, dt, std::nan(""));
     return IT_OK;
 }
 
@@ -717,7 +761,26 @@ int it_reset(it_ctx *c) {
     IT_CK(cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream));
     IT_CK(cudaMemsetAsync(c->d_acc, 0, sizeof(DevAcc), c->stream));
     c->steps = 0;
+    c->t_s = 0.0;
     c->sched_step.clear(); c->sched_tr.clear(); c->sched_ptr = 0;
+    // the time step stays; the log restarts from it
+    c->log_step.assign(1, 0);
+    c->log_dt.assign(1, c->dt);
+    c->log_nmax.assign(1, std::nan(""));
+    return IT_OK;
+}
+
+int it_dt_log(it_ctx *c, int64_t cap, int64_t *first_step, double *dt, double *n_max, int64_t *count) {
+    if (!c || !count || cap < 0) return fail(IT_EINVAL, "bad argument");
+    const int64_t n = (int64_t)c->log_step.size();
+    const int64_t m = std::min(n, cap);
+    if (m > 0 && (!first_step || !dt || !n_max)) return fail(IT_EINVAL, "NULL output array");
+    for (int64_t q = 0; q < m; ++q) {
+        first_step[q] = c->log_step[q];
+        dt[q] = c->log_dt[q];
+        n_max[q] = c->log_nmax[q];
+    }
+    *count = n;
     return IT_OK;
 }
 

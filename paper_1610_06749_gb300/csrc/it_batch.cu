@@ -359,11 +359,13 @@ struct it_batch {
     VecEntry *d_vtab;
     int *d_first, *d_count, *d_simof;
     double *d_slots, *d_mon;
-    size_t tab_cap, stab_cap, vtab_cap, slot_cap, act_cap;
+    float *d_max;                     // per-entry peak density (the dt ladder)
+    size_t tab_cap, stab_cap, vtab_cap, slot_cap, act_cap, max_cap;
     long long chunk;                  // cells per entry
     int vec_cps;                      // CTAs per SM the float4 launch aims for (sets its z split)
     // per simulation
     std::vector<int64_t> steps;
+    std::vector<double> t_s;          // simulated time: the sum of every step's dt
     std::vector<char> active;
     int64_t bstep;                    // steps taken by every active simulation
     cudaStream_t stream;
@@ -532,7 +534,54 @@ int run_segment(it_batch *b, int K) {
     IT_CK(cudaGraphLaunch(b->graph, b->stream));
     b->bstep += K;
     for (int s = 0; s < b->nsim; ++s)
-        if (b->active[s]) b->steps[s] += K;
+        if (b->active[s]) {
+            b->steps[s] += K;
+            b->t_s[s] += b->dt[s] * K;
+        }
+    return IT_OK;
+}
+
+// The doubling ladder of it_run_to_completion, per active simulation with no
+// pulse still to come: one pass for the peak density of every table entry,
+// then each simulation's dt rises to its largest admissible rung.  The step
+// graph reads the descriptors from device memory, so only they change.
+static int ladder_batch(it_batch *b) {
+    const int ne = (int)b->tab.size();
+    if (!ne) return IT_OK;
+    if ((size_t)ne > b->max_cap) {
+        cudaFree(b->d_max);
+        b->d_max = nullptr;
+        b->max_cap = 0;
+        IT_CK(cudaMalloc(&b->d_max, sizeof(float) * ne));
+        b->max_cap = ne;
+    }
+    const int parity = (int)(b->bstep & 1);
+    batch_max_kernel<<<ne, 256, 0, b->stream>>>(b->d_sims, b->d_tab, b->state[parity][0], b->state[parity][1],
+                                                b->d_max);
+    IT_CK(cudaGetLastError());
+    std::vector<float> mx(ne);
+    IT_CK(cudaMemcpyAsync(mx.data(), b->d_max, sizeof(float) * ne, cudaMemcpyDeviceToHost, b->stream));
+    IT_CK(cudaStreamSynchronize(b->stream));
+    int a = 0;
+    for (int s = 0; s < b->nsim; ++s) {
+        if (!b->active[s]) continue;
+        double nmax = -INFINITY;
+        for (int q = b->mfirst[a]; q < b->mfirst[a] + b->mcount[a]; ++q) nmax = std::max(nmax, (double)mx[q]);
+        ++a;
+        const bool pending = b->pulse_done[s] >= 1 && b->pulse_done[s] < b->pulse_count[s];
+        if (pending) continue;
+        const it_sim_desc &d = b->desc[s];
+        it_params p = b->p;
+        p.gap_cm = d.nz * d.dx_cm;
+        p.voltage_V = d.voltage_V;
+        const double nd = ladder_rung(&p, d.dx_cm, b->dt[s], nmax);
+        if (nd > b->dt[s]) {
+            b->dt[s] = nd;
+            coef_f32(&p, d.dx_cm, nd, &b->hs[s].cf);
+            IT_CK(cudaMemcpyAsync(b->d_sims + s, &b->hs[s], sizeof(BatchSim), cudaMemcpyHostToDevice, b->stream));
+        }
+    }
+    IT_CK(cudaStreamSynchronize(b->stream));
     return IT_OK;
 }
 
@@ -575,7 +624,7 @@ void batch_free(it_batch *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->state_base);
     cudaFree(b->d_sims); cudaFree(b->d_acc); cudaFree(b->d_rel);
-    cudaFree(b->d_tab); cudaFree(b->d_slots); cudaFree(b->d_mon);
+    cudaFree(b->d_tab); cudaFree(b->d_slots); cudaFree(b->d_mon); cudaFree(b->d_max);
     cudaFree(b->d_vtab); cudaFree(b->d_stab);
     cudaFree(b->d_first); cudaFree(b->d_count); cudaFree(b->d_simof);
     cudaFree(b->d_plane); cudaFree(b->d_tracks); cudaFree(b->d_wx); cudaFree(b->d_wy);
@@ -603,6 +652,7 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
     b->dx.resize(nsim);
     b->dt.resize(nsim);
     b->steps.assign(nsim, 0);
+    b->t_s.assign(nsim, 0.0);
     b->active.assign(nsim, 1);
     b->pulse_tracks.assign(nsim, {});
     b->pulse_count.assign(nsim, 1);
@@ -923,6 +973,10 @@ int it_batch_run(it_batch *b, double tol, int64_t max_steps, int64_t check_every
             if (rc) return rc;
         }
         if (b->tab.empty()) break;
+        if (b->p.dt_ladder) {
+            rc = ladder_batch(b);
+            if (rc) return rc;
+        }
         rc = run_segment(b, K);
         if (rc) return rc;
         nl += K;
@@ -978,7 +1032,7 @@ int it_batch_tallies(it_batch *b, int32_t sim, it_tallies_t *t) {
     t->f = r > 0 ? (acc[1] + acc[2] + acc[3] + acc[4]) / r : NAN;
     t->steps = b->steps[sim];
     t->dt_s = b->dt[sim];
-    t->t_s = b->dt[sim] * (double)b->steps[sim];
+    t->t_s = b->t_s[sim];
     return IT_OK;
 }
 

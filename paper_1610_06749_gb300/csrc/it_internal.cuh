@@ -126,6 +126,11 @@ struct it_ctx {
     std::vector<double> sched_tr;   // [n][4]
     size_t sched_ptr;
     int64_t steps;
+    double t_s;                        // simulated time: the sum of every step's dt
+    // time-step log: the first step of each dt, the dt and the peak density
+    // that decided it (NaN for the initial dt)
+    std::vector<int64_t> log_step;
+    std::vector<double> log_dt, log_nmax;
     // graph of a fixed segment of steps
     cudaGraphExec_t graph;
     int graph_len;
@@ -177,5 +182,6 @@ int launch_monitor_raw_f32(const float *p, const float *m, size_t cells, double 
                            cudaStream_t s);
 int validate_step_args(const it_params *p, it_grid g, double dx, double dt);
 void coef_f32(const it_params *p, double dx, double dt, Coef<float> *out);
+double ladder_rung(const it_params *p, double dx, double dt, double nmax);
 
 }  // namespace itk

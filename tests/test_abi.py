@@ -90,7 +90,7 @@ int main(void) {
     S(it_params) F(it_params, mu) F(it_params, D) F(it_params, alpha) F(it_params, W_eV)
     F(it_params, gap_cm) F(it_params, voltage_V) F(it_params, precision) F(it_params, lateral_bc)
     F(it_params, scheme) F(it_params, kernel) F(it_params, cfl_safety) F(it_params, react_kappa)
-    F(it_params, n_peak_cm3) F(it_params, space_charge) F(it_params, reserved)
+    F(it_params, n_peak_cm3) F(it_params, space_charge) F(it_params, dt_ladder)
     S(it_tallies_t) F(it_tallies_t, released) F(it_tallies_t, collected_anode)
     F(it_tallies_t, collected_cathode) F(it_tallies_t, lost_lateral) F(it_tallies_t, in_domain)
     F(it_tallies_t, recombined) F(it_tallies_t, f) F(it_tallies_t, t_s) F(it_tallies_t, dt_s)
