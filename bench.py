@@ -16,6 +16,10 @@ Metric: Gcell-updates/s (cells x time steps / s).
             (read and write n+ and n-) / its average duration, against the
             measured HBM copy bandwidth
   cpu_baseline -- the FP64 CPU oracle on the host cores, bounded sample
+  batched -- solves/s of a 256-simulation batch against one context per
+            simulation, with the fixed step and with the doubling dt ladder
+  time_to_solution -- the workload run to completion (upwind), fixed
+            recombination-bound step against the dt ladder
 
 ``--impl reference`` times the oracle (the reference arm of this project) on
 the same workload.  Under torchrun every rank runs an independent replica
@@ -241,8 +245,8 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
         sims.append(dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], dx_cm=d["dx_cm"], voltage_V=d["voltage_V"],
                          n_peak_cm3=B.it_peak_density(tr.let_keV_um, tr.b_cm)))
 
-    def run_batch(idx):
-        bt = B.Batch([sims[q] for q in idx], scheme=scheme)
+    def run_batch(idx, ladder=False):
+        bt = B.Batch([sims[q] for q in idx], scheme=scheme, dt_ladder=ladder)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k, q in enumerate(idx):
@@ -259,6 +263,8 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
         return el, out, launches, (ta, tune_us)
 
     t_all, tal_all, launches, tune = run_batch(list(range(len(sims))))
+    # the same 256 simulations with the doubling dt ladder of the runs to completion
+    t_lad, tal_lad, launches_lad, _ = run_batch(list(range(len(sims))), ladder=True)
     sub = list(range(n_subset))
     t_bsub, tal_bsub, _, _ = run_batch(sub)
     ctxs = [B.Simulation(sims[q]["nx"], sims[q]["ny"], sims[q]["nz"], sims[q]["dx_cm"], sims[q]["voltage_V"],
@@ -288,7 +294,23 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
             "subset": n_subset, "subset_batched_solves_per_s": n_subset / t_bsub,
             "subset_plain_solves_per_s": n_subset / t_plain,
             "speedup_vs_plain": (n_subset / t_bsub) / (n_subset / t_plain),
-            "max_abs_df_vs_plain": df, "df_bound": 1e-3, "scheme": "upwind" if scheme == B.IT_UPWIND else "lax-wendroff"}
+            "max_abs_df_vs_plain": df, "df_bound": 1e-3, "scheme": "upwind" if scheme == B.IT_UPWIND else "lax-wendroff",
+            "ladder": {"solves_per_s": len(sims) / t_lad, "seconds": t_lad, "step_launches": launches_lad,
+                       "speedup_vs_fixed_dt": t_all / t_lad,
+                       "max_abs_df_vs_fixed_dt": max(abs(a.f - b.f) for a, b in zip(tal_lad, tal_all))}}
+
+
+def time_to_solution(V):
+    """The benchmark's pulsed workload run to completion (upwind), with the
+    fixed recombination-bound step and with the doubling dt ladder."""
+    from paper_1610_06749_gb300 import time_to_solution as T
+    from paper_1610_06749_gb300 import binding as B
+    fixed = T.run(V, B.IT_UPWIND, 0.5, False)
+    lad = T.run(V, B.IT_UPWIND, 0.0625, True)
+    keep = ("kappa", "status", "steps", "seconds", "f", "rungs")
+    return {"workload": fixed["workload"], "scheme": "upwind", "fixed_dt": {k: fixed[k] for k in keep},
+            "ladder": {k: lad[k] for k in keep}, "speedup": fixed["seconds"] / lad["seconds"],
+            "abs_df": abs(fixed["f"] - lad["f"]) if fixed["f"] is not None and lad["f"] is not None else None}
 
 
 def surrogate_vs_plain(n_train=2000, n_test=200, epochs=800, plain_sample=40):
@@ -464,6 +486,9 @@ def run_ours(args, ws, rank, local):
     sur = None
     if not args.no_surrogate and rank == 0:
         sur = surrogate_vs_plain()
+    tts = None
+    if not args.no_time_to_solution and rank == 0:
+        tts = time_to_solution(args.voltage)
 
     line = None
     if rank == 0:
@@ -504,6 +529,7 @@ def run_ours(args, ws, rank, local):
             "roofline_continuous_512x512x256": cont,
             "batched": batched,
             "surrogate": sur,
+            "time_to_solution": tts,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -526,6 +552,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain solves/s measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-vs-plain solves/s measurement")
     ap.add_argument("--no-continuous", action="store_true", help="skip the 512x512x256 step-kernel roofline line")
+    ap.add_argument("--no-time-to-solution", action="store_true",
+                    help="skip the run to completion with a fixed step and with the dt ladder")
     ap.add_argument("--launch", default="", help="fixed z-march shape TY,ctas_per_sm,stages,grid (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
