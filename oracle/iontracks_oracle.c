@@ -71,6 +71,8 @@ typedef struct {
  * with n in ions/cm^3 gives V/cm^2. */
 static const double ORC_Q = 1.602176634e-19;
 static const double ORC_EPS0 = 8.8541878128e-14;
+/* sqrt(pi), the normalisation of the 1D profile exp(-u^2/b^2)/(sqrt(pi) b) */
+static const double ORC_SQRT_PI = 1.7724538509055160272981674833411;
 
 static inline size_t pidx(const orc_state *S, int i, int j, int k) {
     return ((size_t)(k + 1) * (size_t)(S->ny + 2) + (size_t)(j + 1)) * (size_t)(S->nx + 2) + (size_t)(i + 1);
@@ -151,6 +153,78 @@ double orc_deposit(orc_state *S, int64_t ntracks, const double *x_cm, const doub
         S->released[s] += released;
     }
     free(plane);
+    return released;
+}
+
+/* Deposit tracks at an angle theta in [0, pi/2] to the field (Fig. setup (a)),
+ * rotated in the x-z plane, each axis through (x_cm, y_cm, d/2).  Eq. (Gaussian)
+ * about the axis: n = N0/(pi b^2) exp(-r^2/b^2), r the distance from the axis.
+ * In the plane of cell centres z_k that distance has the components
+ * u = (x - x0) cos(theta) - (z_k - d/2) sin(theta) and y - y0, so the plane holds
+ * a Gaussian of width b/cos(theta) in x, centred where u = 0.  Each cell receives
+ * its integral over the cell in x and y divided by the cell's area (the cell-
+ * average reading), sampled at the cell centre in z:
+ *   (N0/cos theta) wx wy / dx^2,  wx = (erf(u_hi/b) - erf(u_lo/b)) / 2,
+ * over a window of +-ceil(6 b/(dx cos theta)) cells in x and +-ceil(6 b/dx) in
+ * y.  Periodic faces wrap the window (the images of a tilted track are a
+ * periodic array of parallel tracks, and their densities add), absorbing faces
+ * clip it.  A track within cos(theta) dx/b < 1e-3 of parallel to the
+ * electrodes is one track through the box instead: every cell once, with the
+ * x integral taken at the cell centre, N0/(sqrt(pi) b) exp(-u_c^2/b^2) wy/dx
+ * (the limit cos -> 0; at pi/2 the density does not depend on x).  theta = 0
+ * gives orc_deposit's arithmetic.  Returns the released ions per species. */
+double orc_deposit_angled(orc_state *S, int64_t ntracks, const double *x_cm, const double *y_cm,
+                          const double *let_keV_um, const double *b_cm, const double *theta, double W_eV) {
+    const int nx = S->nx, ny = S->ny, nz = S->nz;
+    const double dx = S->dx, zmid = 0.5 * nz * dx;
+    const size_t plane = (size_t)nx * ny;
+    double *add = (double *)calloc(plane * nz, sizeof(double));
+    for (int64_t t = 0; t < ntracks; ++t) {
+        const double N0 = let_keV_um[t] * 1e7 / W_eV;   /* ions per cm */
+        const double b = b_cm[t], c = cos(theta[t]), sn = sin(theta[t]);
+        const int wy = (int)ceil(6.0 * b / dx);
+        const int jc = (int)floor(y_cm[t] / dx);
+        const int mid = c * dx / b < 1e-3;
+        for (int k = 0; k < nz; ++k) {
+            const double zk = (k + 0.5) * dx;
+            for (int jj = jc - wy; jj <= jc + wy; ++jj) {
+                int j = jj;
+                if (S->lateral_bc == 0) { j %= ny; if (j < 0) j += ny; }
+                else if (j < 0 || j >= ny) continue;
+                const double wyv = gauss_cell_weight(jj * dx, (jj + 1) * dx, y_cm[t], b);
+                double *row = add + (size_t)k * plane + (size_t)j * nx;
+                if (mid) {
+                    for (int i = 0; i < nx; ++i) {
+                        const double u = ((i + 0.5) * dx - x_cm[t]) * c - (zk - zmid) * sn;
+                        row[i] += N0 / (ORC_SQRT_PI * b) * exp(-(u * u) / (b * b)) * wyv / dx;
+                    }
+                    continue;
+                }
+                /* x where u = 0 in this plane, and the window about it */
+                const double xc = x_cm[t] + (zk - zmid) * sn / c;
+                const int wx = (int)ceil(6.0 * b / (dx * c));
+                const int ic = (int)floor(xc / dx);
+                for (int ii = ic - wx; ii <= ic + wx; ++ii) {
+                    int i = ii;
+                    if (S->lateral_bc == 0) { i %= nx; if (i < 0) i += nx; }
+                    else if (i < 0 || i >= nx) continue;
+                    const double wxv = gauss_cell_weight(ii * dx, (ii + 1) * dx, xc, b / c);
+                    row[i] += (N0 / c) * wxv * wyv / (dx * dx);
+                }
+            }
+        }
+    }
+    double sum = 0.0;
+    for (size_t q = 0; q < plane * nz; ++q) sum += add[q];
+    const double released = sum * dx * dx * dx;
+    for (int s = 0; s < 2; ++s) {
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i)
+                    S->n[s][pidx(S, i, j, k)] += add[(size_t)k * plane + (size_t)j * nx + i];
+        S->released[s] += released;
+    }
+    free(add);
     return released;
 }
 

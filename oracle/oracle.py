@@ -69,6 +69,8 @@ def _load():
         lib.orc_set_density.argtypes = [p, dp, dp]
         lib.orc_set_space_charge.argtypes = [p, i]
         lib.orc_space_charge.argtypes = [p, dp]
+        lib.orc_deposit_angled.argtypes = [p, i64, dp, dp, dp, dp, dp, d]
+        lib.orc_deposit_angled.restype = d
         lib.orc_set_dt.argtypes = [p, d]
         lib.orc_set_dt.restype = ctypes.c_int
         lib.orc_time.argtypes = [p]
@@ -151,6 +153,19 @@ class Oracle:
         if n == 0:
             return 0.0
         return _load().orc_deposit(self._h, n, _dptr(x), _dptr(y), _dptr(L), _dptr(b), self.W)
+
+    def deposit_angled(self, x_cm, y_cm, let_keV_um, b_cm, theta_rad) -> float:
+        """Tracks at angle theta in [0, pi/2] to the field, rotated in the x-z
+        plane, axes through (x, y, d/2) (Fig. setup (a)); see
+        orc_deposit_angled.  Returns the released ions per species."""
+        arrs = [np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64)
+                for a in (x_cm, y_cm, let_keV_um, b_cm, theta_rad)]
+        n = arrs[0].size
+        if any(a.size != n for a in arrs):
+            raise ValueError("track arrays differ in length")
+        if n == 0:
+            return 0.0
+        return _load().orc_deposit_angled(self._h, n, *[_dptr(a) for a in arrs], self.W)
 
     def step(self, n: int = 1):
         _load().orc_steps(self._h, int(n))
