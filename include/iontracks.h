@@ -173,6 +173,25 @@ int it_create_ex(it_grid g, double dx_cm, double dt_s, const it_params *p,
 int it_deposit_tracks(it_ctx *ctx, int64_t n, const double *xy_cm,
                       const double *let_keV_um, const double *b_cm);
 
+/* Deposit n tracks at angles theta[i] in [0, pi/2] (radians) to the field
+ * (Fig. setup (a)), each rotated in the x-z plane about an axis through
+ * (xy_cm[2i], xy_cm[2i+1], d/2).  Eq. (Gaussian) about the axis: in the plane
+ * of cell centres z_k the cross-section is a Gaussian of width b/cos(theta)
+ * in x, centred at x + (z_k - d/2) tan(theta), and of width b in y; each cell
+ * receives (N0/cos) wx wy / dx^2 with the cell-integrated weights wx, wy over
+ * +-ceil(6 width/dx) cells (sampled at the cell centre in z).  Periodic faces
+ * wrap the windows (the images of a tilted track are a periodic array of
+ * parallel tracks); absorbing faces clip them.  Within cos(theta) dx/b < 1e-3
+ * of parallel to the electrodes the track is a single column through the box,
+ * each cell once, wx taken at the cell centre.  theta = 0 gives the densities
+ * of it_deposit_tracks.  released grows by the FP64 sum deposited (N0 times
+ * the path length when nothing is clipped).  One thread per cell visits
+ * every track, so the cost is cells x n: for single tracks and small sets
+ * (n <= 2^20).  Synchronous: returns after the deposit has run.  IT_EINVAL as
+ * it_deposit_tracks, or for theta outside [0, pi/2] or NULL. */
+int it_deposit_tracks_angled(it_ctx *ctx, int64_t n, const double *xy_cm, const double *let_keV_um,
+                             const double *b_cm, const double *theta_rad);
+
 /* As it_deposit_tracks, but the tracks are already in device memory as
  * n x 4 doubles (x_cm, y_cm, LET_keV_um, b_cm per track, 16-byte aligned),
  * enqueued on the context stream; nothing is validated on the host, so

@@ -86,6 +86,7 @@ def lib():
             "it_create_ex": (I, [it_grid, D, D, ctypes.POINTER(it_params), P, SZ, P, ctypes.POINTER(P)]),
             "it_deposit_tracks": (I, [P, I64, DP, DP, DP]),
             "it_deposit_tracks_device": (I, [P, I64, P]),
+            "it_deposit_tracks_angled": (I, [P, I64, DP, DP, DP, DP]),
             "it_schedule_tracks": (I, [P, I64, DP, DP, DP, I64P]),
             "it_step": (I, [P, I64]),
             "it_run_to_completion": (I, [P, D, I64, I64, I64P]),
@@ -206,6 +207,13 @@ def it_create_ex(nx, ny, nz, dx_cm, dt_s, p: it_params, dev_state: int, nbytes: 
 def it_deposit_tracks(h, xy_cm, let_keV_um, b_cm):
     xy, L, b = _f64(xy_cm).reshape(-1), _f64(let_keV_um), _f64(b_cm)
     _check(lib().it_deposit_tracks(h, L.size, _dp(xy), _dp(L), _dp(b)))
+
+
+def it_deposit_tracks_angled(h, xy_cm, let_keV_um, b_cm, theta_rad):
+    xy, L, b, th = _f64(xy_cm).reshape(-1), _f64(let_keV_um), _f64(b_cm), _f64(theta_rad)
+    if not (th.size == L.size == b.size and xy.size == 2 * L.size):
+        raise ValueError("track arrays differ in length")
+    _check(lib().it_deposit_tracks_angled(h, L.size, _dp(xy), _dp(L), _dp(b), _dp(th)))
 
 
 def it_deposit_tracks_device(h, n: int, dev_tracks: int):
@@ -567,6 +575,14 @@ class Simulation:
     def deposit(self, x_cm, y_cm, let_keV_um, b_cm):
         xy = np.stack([np.asarray(x_cm, np.float64), np.asarray(y_cm, np.float64)], axis=1)
         it_deposit_tracks(self.h, xy, let_keV_um, b_cm)
+
+    def deposit_angled(self, x_cm, y_cm, let_keV_um, b_cm, theta_rad):
+        """Tracks at angle theta in [0, pi/2] to the field, axes through
+        (x, y, d/2), rotated in the x-z plane (it_deposit_tracks_angled)."""
+        xy = np.stack([np.atleast_1d(np.asarray(x_cm, np.float64)), np.atleast_1d(np.asarray(y_cm, np.float64))],
+                      axis=1)
+        it_deposit_tracks_angled(self.h, xy, np.atleast_1d(let_keV_um), np.atleast_1d(b_cm),
+                                 np.atleast_1d(theta_rad))
 
     def schedule(self, x_cm, y_cm, let_keV_um, b_cm, step_idx):
         xy = np.stack([np.asarray(x_cm, np.float64), np.asarray(y_cm, np.float64)], axis=1)

@@ -148,6 +148,7 @@ static int ctx_free(it_ctx *c) {
     cudaFree(c->d_out);
     cudaFree(c->d_plane);
     cudaFree(c->d_tracks);
+    cudaFree(c->d_angled);
     cudaFree(c->d_wx);
     cudaFree(c->d_wy);
     cudaFree(c->d_err);
@@ -531,6 +532,41 @@ int it_deposit_tracks(it_ctx *c, int64_t n, const double *xy, const double *let,
         packed[4 * t + 3] = b[t];
     }
     return deposit_packed(c, packed, n);
+}
+
+int it_deposit_tracks_angled(it_ctx *c, int64_t n, const double *xy, const double *let, const double *b,
+                             const double *theta) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    int rc = validate_tracks(n, xy, let, b);
+    if (rc || n == 0) return rc;
+    if (!theta) return fail(IT_EINVAL, "theta is NULL");
+    for (int64_t t = 0; t < n; ++t)
+        if (!(theta[t] >= 0.0 && theta[t] <= 1.5707963267948966))
+            return fail(IT_EINVAL, "theta must lie in [0, pi/2]");
+    if (n > (1 << 20)) return fail(IT_EINVAL, "at most 2^20 tilted tracks per call");
+    // track records, then one FP64 partial sum per block of the kernel
+    constexpr int kBlocks = 1216;   // 8 per SM on 152 SMs; fixed, so the sums are deterministic
+    const int64_t need = 5 * n + kBlocks;
+    if (need > c->angled_cap) {
+        cudaFree(c->d_angled);
+        c->d_angled = nullptr;
+        c->angled_cap = 0;
+        IT_CK(cudaMalloc(&c->d_angled, sizeof(double) * need));
+        c->angled_cap = need;
+    }
+    std::vector<double> h((size_t)5 * n);
+    for (int64_t t = 0; t < n; ++t) {
+        h[5 * t + 0] = xy[2 * t];
+        h[5 * t + 1] = xy[2 * t + 1];
+        h[5 * t + 2] = let[t] * 1e7 / c->p.W_eV;   // Eq. (linear_density), ions/cm
+        h[5 * t + 3] = b[t];
+        h[5 * t + 4] = theta[t];
+    }
+    IT_CK(cudaMemcpyAsync(c->d_angled, h.data(), sizeof(double) * 5 * n, cudaMemcpyHostToDevice, c->stream));
+    rc = launch_deposit_angled(c, c->d_angled, n, c->d_angled + 5 * n, kBlocks, c->stream);
+    if (rc) return rc;
+    IT_CK(cudaStreamSynchronize(c->stream));   // the host records are released on return
+    return IT_OK;
 }
 
 int it_deposit_tracks_device(it_ctx *c, int64_t n, const double *dev_tracks) {

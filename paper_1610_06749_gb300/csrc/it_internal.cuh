@@ -116,6 +116,8 @@ struct it_ctx {
     // deposition scratch
     double *d_plane;      // [ny][nx] plane, then the per-tile sums of the deposit
     double *d_tracks;     // [cap][4]: x, y, LET, b
+    double *d_angled;     // [angled_cap][5] tilted tracks (x, y, N0, b, theta), then per-block sums
+    int64_t angled_cap;
     double *d_wx, *d_wy;  // [cap][nx], [cap][ny]
     int64_t track_cap;
     double *h_stage;      // pinned staging for host track uploads [stage_cap][4]
@@ -175,6 +177,7 @@ int launch_finalize(it_ctx *c, cudaStream_t s);
 int launch_monitor(it_ctx *c, cudaStream_t s);
 int launch_deposit(it_ctx *c, int64_t n, cudaStream_t s);   // tracks already in d_tracks
 int launch_zero(void *p, size_t bytes, cudaStream_t s);
+int launch_deposit_angled(it_ctx *c, const double *d_tr, int64_t n, double *d_part, int nblocks, cudaStream_t s);
 int simple_grid(const it_ctx *c);
 int launch_step_simple_raw_f32(const float *ip, const float *im, float *op, float *om, int nx, int ny, int nz,
                                const Coef<float> &cf, bool periodic, double *slots, int nblocks, cudaStream_t s);

@@ -530,6 +530,112 @@ int launch_deposit(it_ctx *c, int64_t n, cudaStream_t s) {
     return IT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// tracks at an angle theta to the field (Fig. setup (a))
+// ---------------------------------------------------------------------------
+
+// Sum of the cell weights (erf(hi/w) - erf(lo/w))/2 of a profile of width w
+// centred at c over the images of cell q in the window [lo_c, hi_c] (cell
+// indices, unwrapped): every q + m n inside it when periodic, q itself when not.
+__device__ __forceinline__ double image_weights(int q, int n, int lo_c, int hi_c, double c, double w, double dx,
+                                                bool periodic) {
+    int m0 = 0, m1 = 0;
+    if (periodic) {
+        // smallest m with q + m n >= lo_c (a ceiling) and largest with
+        // q + m n <= hi_c (a floor); C division truncates toward zero
+        const int a = lo_c - q, bb = hi_c - q;
+        m0 = a >= 0 ? (a + n - 1) / n : -((-a) / n);
+        m1 = bb >= 0 ? bb / n : -((-bb + n - 1) / n);
+    } else if (q < lo_c || q > hi_c) {
+        return 0.0;
+    }
+    double s = 0.0;
+    for (int m = m0; m <= m1; ++m) {
+        const double lo = (double)(q + m * n) * dx;
+        s += 0.5 * (erf((lo + dx - c) / w) - erf((lo - c) / w));
+    }
+    return s;
+}
+
+// One thread per cell (grid-stride, fixed grid), the tracks in order.  Track
+// record [5]: x0, y0, N0 (ions/cm), b, theta.  In the plane of cell centres
+// z_k the tilted column's cross-section is the Gaussian of width b/cos(theta)
+// in x centred at x0 + (z_k - d/2) tan(theta) and of width b in y:
+// (N0/cos) wx wy / dx^2 with the cell weights wx, wy over +-ceil(6 w/dx)
+// cells (images summed when periodic).  Within cos(theta) dx / b < 1e-3 of
+// parallel to the electrodes the track is one column through the box and wx
+// is the cell-centre value dx exp(-u^2/b^2)/(sqrt(pi) b/cos) with
+// u = (x - x0) cos - (z_k - d/2) sin: N0/(sqrt(pi) b) exp(-u^2/b^2) wy/dx.
+// FP32 states add the FP64 sum rounded once, as the parallel deposit does.
+// Each block writes its FP64 sum of the added densities (fixed order).
+template <typename T>
+__global__ void __launch_bounds__(256)
+deposit_angled_kernel(const double *__restrict__ tr, int n, int nx, int ny, int nz, double dx, int periodic,
+                      T *__restrict__ p, T *__restrict__ m, double *__restrict__ part) {
+    __shared__ double red[32];
+    const double zmid = 0.5 * nz * dx;
+    const double sqrt_pi = 1.7724538509055160272981674833411;
+    const size_t cells = (size_t)nx * ny * nz;
+    double bsum[1] = {0.0};
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < cells;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % (size_t)nx);
+        const int j = (int)((idx / (size_t)nx) % (size_t)ny);
+        const int k = (int)(idx / ((size_t)nx * ny));
+        const double zk = (k + 0.5) * dx;
+        double v = 0.0;
+        for (int t = 0; t < n; ++t) {
+            const double x0 = tr[5 * t], y0 = tr[5 * t + 1], N0 = tr[5 * t + 2], b = tr[5 * t + 3];
+            const double th = tr[5 * t + 4];
+            const int wy = (int)ceil(6.0 * b / dx), jc = (int)floor(y0 / dx);
+            const double sy = image_weights(j, ny, jc - wy, jc + wy, y0, b, dx, periodic);
+            if (sy == 0.0) continue;
+            const double c = cos(th), sn = sin(th);
+            if (c * dx / b < 1e-3) {
+                const double u = ((i + 0.5) * dx - x0) * c - (zk - zmid) * sn;
+                v += N0 / (sqrt_pi * b) * exp(-(u * u) / (b * b)) * sy / dx;
+            } else {
+                const double xc = x0 + (zk - zmid) * sn / c;
+                const int wx = (int)ceil(6.0 * b / (dx * c)), ic = (int)floor(xc / dx);
+                const double sx = image_weights(i, nx, ic - wx, ic + wx, xc, b / c, dx, periodic);
+                v += (N0 / c) * sx * sy / (dx * dx);
+            }
+        }
+        if (v != 0.0) {
+            if constexpr (sizeof(T) == 4) {
+                const float vf = __double2float_rn(v);
+                p[idx] = __fadd_rn(p[idx], vf);
+                m[idx] = __fadd_rn(m[idx], vf);
+            } else {
+                p[idx] += v;
+                m[idx] += v;
+            }
+            bsum[0] += v;
+        }
+    }
+    block_sum<1>(bsum, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bsum[0];
+}
+
+int launch_deposit_angled(it_ctx *c, const double *d_tr, int64_t n, double *d_part, int nblocks, cudaStream_t s) {
+    if (n <= 0) return IT_OK;
+    const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
+    const int per = c->p.lateral_bc == IT_PERIODIC ? 1 : 0;
+    if (c->prec == IT_FP32)
+        deposit_angled_kernel<float><<<nblocks, 256, 0, s>>>(d_tr, (int)n, nx, ny, nz, c->dx, per,
+                                                             (float *)c->n[c->cur][0], (float *)c->n[c->cur][1],
+                                                             d_part);
+    else
+        deposit_angled_kernel<double><<<nblocks, 256, 0, s>>>(d_tr, (int)n, nx, ny, nz, c->dx, per,
+                                                              (double *)c->n[c->cur][0],
+                                                              (double *)c->n[c->cur][1], d_part);
+    IT_CK(cudaGetLastError());
+    const double vol = c->dx * c->dx * c->dx;
+    deposit_released_kernel<<<1, 256, 0, s>>>(d_part, (size_t)nblocks, vol, c->d_acc);
+    IT_CK(cudaGetLastError());
+    return IT_OK;
+}
+
 int launch_zero(void *p, size_t bytes, cudaStream_t s) {
     IT_CK(cudaMemsetAsync(p, 0, bytes, s));
     return IT_OK;
