@@ -186,13 +186,17 @@ class Oracle:
         peak density, capped at cfl_safety times the Eq. (vNeum) step.
 
         Returns (steps taken, completed, log) where log lists
-        (step, dt, n_max) for the initial dt and every change."""
+        (step, dt, n_max) for the initial dt and every change.  Raises
+        FloatingPointError when a check finds the state not finite (the
+        library's IT_EUNSTABLE), rather than stepping on to max_steps."""
         start = self.tallies().steps
         log = [(start, self.dt, float("nan"))]
         cap = cfl_safety * dt_von_neumann(self.dx, self.V, self.gap, self.mu, self.D, self.scheme)
         while True:
             t = self.tallies()
             rel = float(t.released.sum())
+            if not math.isfinite(float(t.in_domain.sum()) + t.recombined):
+                raise FloatingPointError(f"oracle: state is not finite at step {t.steps}")
             if rel > 0 and float(t.in_domain.sum()) / rel < tol:
                 return t.steps - start, True, log
             if rel == 0:

@@ -803,3 +803,20 @@ def test_track_parallel_to_the_electrodes_follows_jaffe_angle():
         assert done
         gaps.append(abs(O.tallies().f - fj))
     assert gaps[0] < 3e-3 and gaps[1] < 1e-3 and gaps[1] < gaps[0]
+
+
+def test_run_to_completion_stops_on_a_state_that_is_not_finite():
+    # Lax-Wendroff at the recombination-bound step on a dense pulse diverges:
+    # at the small Courant number its undershoots make -alpha n+ n- a
+    # source.  The run must stop at the first check that sees it, as the
+    # library's IT_EUNSTABLE does, not step on to max_steps.
+    nx, ny, nz, dx, V = 24, 24, 40, 5e-4, 50.0
+    tr = synth.uniform_tracks(11, 6, nx * dx, ny * dx, 1e-3, let="loguniform")
+    tr.let_keV_um[:] = np.maximum(tr.let_keV_um, 100.0)
+    npk = o.peak_track_density(tr.let_keV_um, tr.b_cm)
+    dt = o.dt_rule(dx, V, nz * dx, MU, DD, ALPHA, n_peak=npk, kappa=0.25)
+    O = o.Oracle(nx, ny, nz, dx, dt, mu=MU, D=DD, alpha=ALPHA, voltage_V=V)
+    O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+    with pytest.raises(FloatingPointError):
+        O.run_to_completion(1e-6, 200_000, 64)
+    assert O.tallies().steps < 5000
