@@ -164,3 +164,18 @@ def test_create_without_gpu_fails_loudly(L):
     with pytest.raises(B.ItError) as e:
         B.it_create(48, 48, 100, 2e-4, 0.0, p)
     assert e.value.code == B.IT_ECUDA
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu(L):
+    import ctypes
+    # a NULL context is refused before anything reaches the device
+    xy = (ctypes.c_double * 2)(1e-3, 1e-3)
+    one = (ctypes.c_double * 1)(1.0)
+    assert L.it_deposit_tracks_angled(None, 1, xy, one, one, one) == B.IT_EINVAL
+    n = ctypes.c_int64()
+    assert L.it_dt_log(None, 0, None, None, None, ctypes.byref(n)) == B.IT_EINVAL
+    # dt_ladder must be 0 or 1
+    p = B.it_params_default(gap_cm=0.02, voltage_V=200.0, dt_ladder=2)
+    with pytest.raises(B.ItError) as e:
+        B.it_create(48, 48, 100, 2e-4, 0.0, p)
+    assert e.value.code == B.IT_EINVAL
