@@ -271,6 +271,17 @@ int it_set_density(it_ctx *ctx, const void *plus, const void *minus, size_t byte
  * state actually deposited.  The time-step log restarts from the new dt. */
 int it_retime(it_ctx *ctx, double dt_s);
 
+/* One check of the dt ladder of it_run_to_completion, on the host: the dt
+ * that a check with peak density n_max (ions/cm^3) picks after dt_s, for a
+ * grid of spacing dx_cm under *p (gap_cm and voltage_V set the field).
+ * *dt_out = min(cap, dt_s 2^j), j >= 0 the largest integer with
+ * alpha (dt_s 2^j) n_max <= react_kappa (and, with space charge,
+ * max(mu) q/eps0 (dt_s 2^j) n_max <= react_kappa); never below dt_s; cap =
+ * cfl_safety times the Eq. (vNeum) step.  No device is needed.  IT_EINVAL for
+ * NULL pointers, dx_cm or gap_cm <= 0, dt_s <= 0 or a negative or non-finite
+ * n_max. */
+int it_ladder_dt(const it_params *p, double dx_cm, double dt_s, double n_max, double *dt_out);
+
 /* The time-step log: entry q holds the first step run with a dt
  * (first_step[q]), that dt (dt[q], s) and the peak density that decided it
  * (n_max[q], ions/cm^3; NaN for a dt set at creation, it_retime, it_reset or

@@ -80,6 +80,7 @@ def lib():
             "it_last_error": (ctypes.c_char_p, []),
             "it_params_default": (I, [ctypes.POINTER(it_params)]),
             "it_auto_dt": (I, [ctypes.POINTER(it_params), D, DP]),
+            "it_ladder_dt": (I, [ctypes.POINTER(it_params), D, D, D, DP]),
             "it_peak_density": (I, [I64, DP, DP, D, DP]),
             "it_state_bytes": (I, [it_grid, ctypes.c_int32, ctypes.POINTER(SZ)]),
             "it_create": (I, [it_grid, D, D, ctypes.POINTER(it_params), ctypes.POINTER(P)]),
@@ -170,6 +171,12 @@ def it_params_default(**kw) -> it_params:
         else:
             setattr(p, k, v)
     return p
+
+
+def it_ladder_dt(p: it_params, dx_cm: float, dt_s: float, n_max: float) -> float:
+    out = ctypes.c_double()
+    _check(lib().it_ladder_dt(ctypes.byref(p), float(dx_cm), float(dt_s), float(n_max), ctypes.byref(out)))
+    return out.value
 
 
 def it_auto_dt(p: it_params, dx_cm: float) -> float:

@@ -386,6 +386,15 @@ int it_auto_dt(const it_params *p, double dx_cm, double *dt_out) {
     return IT_OK;
 }
 
+int it_ladder_dt(const it_params *p, double dx_cm, double dt_s, double n_max, double *dt_out) {
+    if (!p || !dt_out) return fail(IT_EINVAL, "NULL argument");
+    if (!(std::isfinite(dx_cm) && dx_cm > 0) || !(p->gap_cm > 0)) return fail(IT_EINVAL, "dx and gap must be > 0");
+    if (!(std::isfinite(dt_s) && dt_s > 0)) return fail(IT_EINVAL, "dt must be positive and finite");
+    if (!(std::isfinite(n_max) && n_max >= 0)) return fail(IT_EINVAL, "n_max must be finite and >= 0");
+    *dt_out = ladder_rung(p, dx_cm, dt_s, n_max);
+    return IT_OK;
+}
+
 int it_peak_density(int64_t n, const double *let, const double *b, double W_eV, double *out) {
     if (!out || n < 0 || (n > 0 && (!let || !b)) || !(W_eV > 0)) return fail(IT_EINVAL, "bad argument");
     double best = 0.0;

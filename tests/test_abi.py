@@ -179,3 +179,33 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(L):
     with pytest.raises(B.ItError) as e:
         B.it_create(48, 48, 100, 2e-4, 0.0, p)
     assert e.value.code == B.IT_EINVAL
+
+
+@pytest.mark.parametrize("space_charge", [0, 1])
+def test_ladder_rule_matches_the_oracle(L, space_charge):
+    # The library's rung (it_ladder_dt, the rule of it_run_to_completion) and
+    # the oracle's ladder_dt are written independently.  Below the Eq.
+    # (vNeum) cap a rung is dt times a power of two, so the two agree exactly;
+    # at the cap they agree to the rounding of the two dt_vN evaluations.
+    rng = np.random.default_rng(23)
+    rungs = capped = 0
+    for _ in range(4000):
+        dx = 10.0 ** rng.uniform(-4.5, -3)
+        nz = int(rng.integers(10, 400))
+        V = float(rng.uniform(10, 500))
+        scheme = int(rng.integers(0, 2))
+        kappa = float(rng.choice([0.5, 0.25, 0.0625]))
+        p = B.it_params_default(gap_cm=nz * dx, voltage_V=V, scheme=scheme, react_kappa=kappa,
+                                space_charge=space_charge)
+        cap = o.dt_von_neumann(dx, V, nz * dx, (1.73, 1.87), (0.037, 0.037), scheme)
+        dt = cap * 10.0 ** rng.uniform(-4, 0)
+        nmax = 10.0 ** rng.uniform(8, 15) if rng.random() < 0.95 else 0.0
+        got = B.it_ladder_dt(p, dx, dt, nmax)
+        want = o.ladder_dt(dt, nmax, 1.6e-6, cap, kappa, 1.87, bool(space_charge))
+        if want < cap * (1 - 1e-12):
+            assert got == want
+            rungs += got > dt
+        else:
+            assert got == pytest.approx(want, rel=1e-14)
+            capped += 1
+    assert rungs > 500 and capped > 100
