@@ -183,7 +183,10 @@ int it_deposit_tracks(it_ctx *ctx, int64_t n, const double *xy_cm,
  * wrap the windows (the images of a tilted track are a periodic array of
  * parallel tracks); absorbing faces clip them.  Within cos(theta) dx/b < 1e-3
  * of parallel to the electrodes the track is a single column through the box,
- * each cell once, wx taken at the cell centre.  theta = 0 gives the densities
+ * each cell once, wx taken at the cell centre.  With periodic faces the two
+ * descriptions differ at that switch by design: just outside it the images of
+ * a track that crosses the gap over d tan(theta) in x stack up as many
+ * parallel tracks; with absorbing faces the two forms agree there.  theta = 0 gives the densities
  * of it_deposit_tracks.  released grows by the FP64 sum deposited (N0 times
  * the path length when nothing is clipped).  One thread per cell visits
  * every track, so the cost is cells x n: for single tracks and small sets

@@ -820,3 +820,25 @@ def test_run_to_completion_stops_on_a_state_that_is_not_finite():
     with pytest.raises(FloatingPointError):
         O.run_to_completion(1e-6, 200_000, 64)
     assert O.tallies().steps < 5000
+
+
+def test_angled_deposit_is_continuous_across_the_parallel_to_electrodes_switch():
+    # Absorbing faces, so a tilted track has no periodic images: just above
+    # and just below cos(theta) dx / b = 1e-3 the erf form and the
+    # cell-centre form describe the same single column (its x profile is
+    # b/cos = 200 b wide, nearly flat across the box).  The midpoint rule
+    # differs from the cell integral by about (cos dx/b)^2/24 relative and
+    # the angles by 1e-6 relative in cos, both far below 1e-6.  (With
+    # periodic faces the erf form would sum the images of the tilted track,
+    # a stack of parallel tracks, while the near-parallel form is one track
+    # by definition.)
+    nx, ny, nz, dx, b = 8, 30, 40, 2e-4, 1e-3
+    c_switch = 1e-3 * b / dx
+    out = []
+    for c in (c_switch * (1 + 1e-6), c_switch * (1 - 1e-6)):
+        O = o.Oracle(nx, ny, nz, dx, 1e-9, lateral_bc=o.LATERAL_ABSORBING)
+        O.deposit_angled([0.5 * nx * dx], [0.5 * ny * dx], [5.0], [b], [math.acos(c)])
+        out.append(O.density(0))
+    scale = np.max(out[1])
+    assert scale > 0
+    assert np.max(np.abs(out[0] - out[1])) <= 1e-6 * scale
