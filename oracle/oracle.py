@@ -178,8 +178,8 @@ class Oracle:
 
     def run_to_completion(self, tol=1e-6, max_steps=10_000_000, check_every=64, ladder=False, kappa=0.5,
                           cfl_safety=1.0):
-        """Step until the tracks are dragged apart (Sec. Implementation,
-        P:246): at every check (the first before any step, then every
+        """Step until the tracks are dragged apart (end of Sec.
+        Implementation): at every check (the first before any step, then every
         check_every steps) stop when the ions left in the domain are below
         tol of the released ones (or nothing was released).  With
         ladder=True each check first raises dt by ladder_dt from the state's
@@ -227,32 +227,56 @@ class Oracle:
             self.step(1)
 
     def run_to_steady_state(self, x_cm, y_cm, let, b, step_idx, window: int, tol: float, max_steps: int):
-        """Continuous beam to steady state (Sec. Implementation):
-        windows of `window` steps with the scheduled arrivals, until the
-        efficiency of the ions that left the domain in a window,
-        f_ss = dCol / (dCol + 2 dRec + dLost), changes by less than tol
-        between two windows, or until the next window would pass max_steps.
-        Returns (f_ss of the last window, stop: 0 steady / 1 step limit,
-        steps taken)."""
-        def gone(t):
-            return float(t.collected.sum()), float(t.recombined), float(t.lost_lateral.sum())
-        start = self.tallies().steps
-        c0, r0, l0 = gone(self.tallies())
-        f_prev = f_cur = float("nan")
-        n = 0
+        """Continuous beam to steady state (Sec. Implementation, "Distribution
+        of ion tracks"), reading "f stable to tol over a window of steps" on
+        the ions that have left the domain since the call began: windows of
+        `window` steps with the scheduled arrivals; after window w the
+        aggregate efficiency is F_w = Col / (Col + 2 Rec + Lost), both
+        species, Col collected at the electrodes, Rec recombined pairs (two
+        ions each), Lost through absorbing faces, all counted since the call
+        began.  The run stops after the first window w >= 2 with
+        |F_w - F_{w-1}| < tol that is judged: the window's own departures
+        are positive and at least half of (ions released since the call
+        began) / w, and the departures since the call began are at least
+        half of those released.  Otherwise it ends when the next window would
+        pass max_steps.
+
+        Returns a dict: f_ss (= F of the last window), f_ss_stderr (ratio
+        estimator over 10 batches of consecutive windows, NaN below 10
+        windows), f_window (the last window's own Col / departed), departed,
+        released, windows, steps, stop (0 steady, 1 step limit)."""
+        def state(t):
+            return float(t.collected.sum()), float(t.recombined), float(t.lost_lateral.sum()), float(t.released.sum())
+
+        t = self.tallies()
+        start = t.steps
+        c_s, r_s, l_s, rel_s = state(t)
+        per_window = []                       # (collected, departed) in each window
+        prev = (c_s, r_s, l_s)
+        F_prev = F = f_win = float("nan")
+        C = G = Rel = 0.0
+        stop = 1
         while self.tallies().steps - start + window <= max_steps:
-            s0 = self.tallies().steps
-            self.run_schedule(x_cm, y_cm, let, b, step_idx, window, start_step=s0)
-            c1, r1, l1 = gone(self.tallies())
-            dc, dr, dl = c1 - c0, r1 - r0, l1 - l0
-            c0, r0, l0 = c1, r1, l1
-            den = dc + 2.0 * dr + dl
-            f_cur = dc / den if den != 0.0 else float("nan")
-            n += 1
-            if n >= 2 and np.isfinite(f_cur) and np.isfinite(f_prev) and abs(f_cur - f_prev) < tol:
-                return f_cur, 0, self.tallies().steps - start
-            f_prev = f_cur
-        return f_cur, 1, self.tallies().steps - start
+            self.run_schedule(x_cm, y_cm, let, b, step_idx, window, start_step=self.tallies().steps)
+            c1, r1, l1, rel1 = state(self.tallies())
+            dc, dr, dl = c1 - prev[0], r1 - prev[1], l1 - prev[2]
+            prev = (c1, r1, l1)
+            g = dc + 2.0 * dr + dl
+            per_window.append((dc, g))
+            f_win = dc / g if g != 0.0 else float("nan")
+            C = c1 - c_s
+            G = C + 2.0 * (r1 - r_s) + (l1 - l_s)
+            Rel = rel1 - rel_s
+            F = C / G if G != 0.0 else float("nan")
+            w = len(per_window)
+            judged = g > 0.0 and g >= 0.5 * Rel / w and G >= 0.5 * Rel
+            if judged and w >= 2 and math.isfinite(F) and math.isfinite(F_prev) and abs(F - F_prev) < tol:
+                stop = 0
+                break
+            F_prev = F
+        se = ratio_batch_stderr([p[0] for p in per_window], [p[1] for p in per_window])
+        return {"f_ss": F, "f_ss_stderr": se, "f_window": f_win, "departed": G, "released": Rel,
+                "windows": len(per_window), "steps": self.tallies().steps - start, "stop": stop}
 
     def tallies(self) -> Tallies:
         lib = _load()
@@ -279,6 +303,25 @@ class Oracle:
         p = np.ascontiguousarray(np.broadcast_to(plus, shape), dtype=np.float64)
         m = np.ascontiguousarray(np.broadcast_to(minus, shape), dtype=np.float64)
         _load().orc_set_density(self._h, _dptr(p), _dptr(m))
+
+
+def ratio_batch_stderr(c, g, nb: int = 10) -> float:
+    """Standard error of the ratio F = sum(c) / sum(g) of per-window sums by
+    batch means: the windows are cut into nb batches of consecutive windows
+    (batch k holds windows [k n / nb, (k+1) n / nb)), and with the batch sums
+    C_k, G_k and residuals e_k = C_k - F G_k (which sum to zero),
+    SE = sqrt(nb / (nb - 1) * sum e_k^2) / sum(g) -- the delta-method error of
+    a ratio estimator.  NaN below nb windows or when sum(g) is 0."""
+    n = len(c)
+    G = float(sum(g))
+    if n < nb or G == 0.0:
+        return float("nan")
+    F = float(sum(c)) / G
+    resid = []
+    for k in range(nb):
+        lo, hi = k * n // nb, (k + 1) * n // nb
+        resid.append(float(sum(c[lo:hi])) - F * float(sum(g[lo:hi])))
+    return math.sqrt(nb / (nb - 1) * sum(e * e for e in resid)) / G
 
 
 # ---------------------------------------------------------------------------

@@ -11,7 +11,7 @@ run to completion at three field strengths:
 
 The figures print no values, so the table is the reproduction; run with
 ``-s`` to print it.  D and mu in the closed forms are the means of the two
-species (P:180).
+species (Sec. "The Jaffe theory", the text under Eq. Jaffe_noangle).
 
 Jaffe's closed forms describe initial recombination, so each run is
 compared through f_rec = 1 - recombined/released (per species), the

@@ -415,6 +415,39 @@ def test_single_track_jaffe_gap_shrinks_with_dx():
     assert e10 < 0.3 * e5 and e10 < 5e-5
 
 
+def test_config1_jaffe_gap_is_a_converged_gap_not_discretisation():
+    # The 100 keV/um single track (y1 = 0.02).  tests/golden/single_track_dx_sweep.json
+    # holds the oracle's f at dx = b/5, b/10 and b/20 (written by the script
+    # beside it); the b/5 value is rerun here.  The successive changes of f
+    # shrink (the scheme converges; about first order, since the step is
+    # drift-limited, dt ~ dx, and the explicit recombination is first order
+    # in dt), while the gap to Eq. (Jaffe_noangle) grows towards ~0.058: the
+    # gap is the Gaussian-shape ansatz behind Jaffe's form failing at this
+    # LET, not discretisation error.
+    g = _gold("single_track_dx_sweep.json")
+    r5 = g["runs"][0]
+    dt = o.dt_rule(r5["dx_cm"], g["voltage_V"], g["gap_cm"], n_peak=o.peak_track_density([g["LET_keV_um"]],
+                                                                                        [g["b_cm"]]))
+    assert dt == r5["dt_s"]
+    O = o.Oracle(r5["nx"], r5["ny"], r5["nz"], r5["dx_cm"], dt, voltage_V=g["voltage_V"],
+                 lateral_bc=o.LATERAL_ABSORBING)
+    c = 0.5 * r5["nx"] * r5["dx_cm"]
+    O.deposit([c], [c], [g["LET_keV_um"]], [g["b_cm"]])
+    steps, done, _ = O.run_to_completion(tol=1e-9, check_every=32)
+    assert done and steps == r5["steps"]
+    assert O.tallies().f == pytest.approx(r5["f"], abs=1e-12)
+    fj = o.jaffe_parallel(g["LET_keV_um"], g["b_cm"], g["gap_cm"], g["voltage_V"] / g["gap_cm"],
+                          0.5 * sum(MU), 0.5 * sum(DD), ALPHA)
+    assert fj == pytest.approx(g["f_jaffe"], abs=1e-14)
+    f = [r["f"] for r in g["runs"]]
+    d1, d2 = f[1] - f[0], f[2] - f[1]
+    assert 0.0 < d2 < 0.7 * d1
+    r = d2 / d1
+    f_inf = f[2] + d2 * r / (1.0 - r)          # geometric (Richardson) extrapolation
+    assert 0.05 < f_inf - fj < 0.07
+    assert f[0] - fj < f[1] - fj < f[2] - fj
+
+
 def test_proton_initial_recombination_below_0p1_percent():
     # Table 1 proton (LET 7.76e-4 keV/um, b = 10 um): 1 - f < 1e-3
     g = _gold("paper_tables.json")
@@ -480,7 +513,8 @@ def test_many_overlapping_low_let_tracks_follow_boag():
     # once: initial recombination is negligible, the tracks merge into a
     # nearly uniform charge density n = released / (Lx Ly d), and f follows
     # Boag's pulsed-beam f = ln(1+u)/u with u = alpha n d^2 / ((mu+ + mu-) V)
-    # (P:211).  Track structure and the diffusion of the fronts are
+    # (the 2VM formula of Sec. "The free-electron component" at p = 0, used
+    # again in Sec. "Comparison with Boag's free-electron models").  Track structure and the diffusion of the fronts are
     # the residual.
     nx, ny, nz, dx, V, b = 24, 24, 40, 5e-4, 200.0, 1e-3
     d = nz * dx
@@ -550,16 +584,60 @@ def test_steady_state_of_a_sparse_track_train_is_the_single_track_f():
     steps = np.arange(n, dtype=np.int64) * P
     xs, ys = np.full(n, 0.5 * nx * dx), np.full(n, 0.5 * ny * dx)
     train = o.Oracle(nx, ny, nz, dx, dt, **kw)
-    f_ss, stop, done = train.run_to_steady_state(xs, ys, np.full(n, let), np.full(n, b), steps, P, 1e-9, n * P)
-    assert stop == 0 and done == 2 * P
-    assert f_ss == pytest.approx(f1, rel=1e-11)
+    r = train.run_to_steady_state(xs, ys, np.full(n, let), np.full(n, b), steps, P, 1e-9, n * P)
+    assert r["stop"] == 0 and r["steps"] == 2 * P and r["windows"] == 2
+    assert r["f_ss"] == pytest.approx(f1, rel=1e-11)
+    assert r["f_window"] == pytest.approx(f1, rel=1e-11)
+    # with tol = 0 the rule never holds: all 12 windows run, each holding one
+    # track's ions, so every batch has the same efficiency and the batch-means
+    # error vanishes
+    n = 12
+    steps = np.arange(n, dtype=np.int64) * P
+    xs, ys = np.full(n, 0.5 * nx * dx), np.full(n, 0.5 * ny * dx)
+    train = o.Oracle(nx, ny, nz, dx, dt, **kw)
+    r = train.run_to_steady_state(xs, ys, np.full(n, let), np.full(n, b), steps, P, 0.0, n * P)
+    assert r["stop"] == 1 and r["windows"] == n
+    assert r["f_ss"] == pytest.approx(f1, rel=1e-11)
+    assert r["f_ss_stderr"] < 1e-12
+    assert r["released"] == pytest.approx(n * t1.released.sum(), rel=1e-12)
+    assert r["departed"] == pytest.approx(r["released"], rel=1e-9)
+
+
+def test_steady_state_runner_does_not_stop_on_idle_windows():
+    # One track, then nothing: once it has left, every window is idle and the
+    # aggregate no longer moves.  An idle window carries no departures, so it
+    # is not judged and the run ends at the step limit (a rule that judged it
+    # would call this steady after the track's life).
+    nx, nz, dx, V, let, b = 16, 20, 5e-4, 300.0, 300.0, 1e-3
+    kw = dict(mu=MU, D=DD, alpha=ALPHA, voltage_V=V, lateral_bc=o.LATERAL_ABSORBING, scheme=o.SCHEME_UPWIND)
+    dt = o.dt_rule(dx, V, nz * dx, n_peak=o.peak_track_density([let], [b]), scheme=o.SCHEME_UPWIND)
+    O = o.Oracle(nx, nx, nz, dx, dt, **kw)
+    r = O.run_to_steady_state([0.5 * nx * dx], [0.5 * nx * dx], [let], [b], np.zeros(1, dtype=np.int64),
+                              100, 1e-3, 1200)
+    assert r["stop"] == 1 and r["windows"] == 12
+    assert 0.0 < r["f_ss"] < 1.0
 
 
 def test_steady_state_runner_stops_at_the_step_limit():
     # a window longer than the limit: no window runs, the limit is reported
     O = o.Oracle(8, 8, 8, 5e-4, 1e-9, mu=MU, D=DD, alpha=ALPHA, voltage_V=100.0)
-    f_ss, stop, done = O.run_to_steady_state([], [], [], [], np.zeros(0, dtype=np.int64), 50, 1e-5, 40)
-    assert stop == 1 and done == 0 and math.isnan(f_ss)
+    r = O.run_to_steady_state([], [], [], [], np.zeros(0, dtype=np.int64), 50, 1e-5, 40)
+    assert r["stop"] == 1 and r["steps"] == 0 and r["windows"] == 0 and math.isnan(r["f_ss"])
+
+
+def test_ratio_batch_stderr_reduces_to_the_standard_error_of_a_mean():
+    # with equal window weights the ratio estimator is the mean of the window
+    # values, and its batch-means error (one window per batch) is the
+    # textbook s / sqrt(n): values alternating 0.1, 0.3 have s = sqrt(0.1/9)
+    se = o.ratio_batch_stderr([0.1, 0.3] * 5, [1.0] * 10)
+    assert se == pytest.approx(math.sqrt(0.1 / 9.0) / math.sqrt(10.0), rel=1e-14)
+    # proportional windows give zero; fewer than 10 windows give NaN
+    assert o.ratio_batch_stderr([0.2 * k for k in range(1, 21)], [float(k) for k in range(1, 21)]) < 1e-15
+    assert math.isnan(o.ratio_batch_stderr([0.1] * 9, [1.0] * 9))
+    # batches of two windows: sums per batch
+    c = [0.1, 0.1, 0.3, 0.3] * 5
+    assert o.ratio_batch_stderr(c, [1.0] * 20) == pytest.approx(
+        math.sqrt(10.0 / 9.0 * 10 * 0.2 ** 2) / 20.0, rel=1e-14)
 
 
 # --------------------------------------------------------------------------
@@ -608,7 +686,7 @@ def test_space_charge_leaves_a_neutral_plasma_alone():
 def test_space_charge_conservation_and_proton_invariance():
     # With the term on, the balance closes with its tally:
     # released + added = in domain + collected + lost + recombined.  At a
-    # proton-like LET the term changes f by less than 1e-4.
+    # proton-like LET the term changes f by less than 1e-4 (Sec. Conclusions: negligible for protons).
     nx, ny, nz, dx, V = 16, 16, 20, 5e-4, 200.0
     for let, check_f in ((300.0, False), (2e-3, True)):
         npk = o.peak_track_density([let], [1e-3])
