@@ -234,24 +234,42 @@ int it_step(it_ctx *ctx, int64_t n_steps);
 int it_run_to_completion(it_ctx *ctx, double tol, int64_t max_steps,
                          int64_t check_every, int64_t *steps_done);
 
-/* Continuous beam (Poisson arrivals scheduled with it_schedule_tracks; Sec.
- * Implementation): step in windows of window_steps until the
- * steady-state collection efficiency of two successive windows differs by
- * less than tol, or until the next whole window would pass max_steps more
- * steps.  The efficiency of a window counts the ions that left the domain
- * during it, f_ss = dCol / (dCol + 2 dRec + dLost), over both species: dCol
- * collected at either electrode, dRec recombined pairs (two ions each), dLost
- * lost through absorbing lateral faces.  The cumulative f of it_tallies
- * carries the ions still in flight; f_ss does not.  *f_ss (may be NULL)
- * receives the last window's value (NaN when no ion left the domain in it),
- * *stop (may be NULL) 0 when the steady state ended the run and 1 when the
- * step limit did, *steps_done (may be NULL) the steps taken.  Returns
- * IT_EUNSTABLE if the state went non-finite; reaching the step limit is not
- * an error.  Windows in which no pair recombined and nothing was lost have
- * f_ss = 1: two such windows in a row (sparse arrivals) meet the rule
- * trivially. */
-int it_run_to_steady_state(it_ctx *ctx, int64_t window_steps, double tol, int64_t max_steps, double *f_ss,
-                           int *stop, int64_t *steps_done);
+/* Result of it_run_to_steady_state. */
+typedef struct {
+    double f_ss;          /* departure efficiency of every ion that left the domain since the
+                             call began: Col / (Col + 2 Rec + Lost) over both species */
+    double f_ss_stderr;   /* its standard error: the ratio estimator over 10 batches of
+                             consecutive windows (NaN below 10 windows); batches shorter than
+                             an ion's transit underestimate it */
+    double f_window;      /* the last window's own departure efficiency (NaN: nothing left) */
+    double departed;      /* ions that left the domain since the call began (Col + 2 Rec + Lost) */
+    double released;      /* ions released since the call began */
+    int64_t windows;      /* windows run */
+    int64_t steps;        /* steps taken */
+    int32_t stop;         /* 0: the steady-state rule ended the run; 1: the step limit did */
+    int32_t pad_;
+} it_steady_t;
+
+/* Continuous beam run to steady state (Poisson arrivals scheduled with
+ * it_schedule_tracks; Sec. Implementation, "Distribution of ion tracks"):
+ * step in windows of window_steps, the caller having run any warm-up
+ * before the call.  The cumulative f of it_tallies carries the ions still
+ * in flight, so the rule judges the ions that have left the domain since
+ * the call began: the aggregate f_ss = Col / (Col + 2 Rec + Lost), Col the
+ * ions collected at either electrode, Rec the recombined pairs (two ions
+ * each), Lost the ions lost through absorbing lateral faces.  The run stops
+ * at the end of the first window, from the second on, after which f_ss has
+ * moved by less than tol over that window ("f stable to tol over
+ * window_steps steps"), provided the window carried departures of at least
+ * half the mean release per window since the call began and the aggregate
+ * covers at least half of the ions released since then (an idle window of
+ * a sparse beam does not move f_ss and must not end the run); or when the
+ * next whole window would pass max_steps more steps.  The run's precision
+ * is f_ss_stderr, not tol.  *out (may be NULL) receives the result.
+ * Returns IT_EUNSTABLE if the state went non-finite; reaching the step
+ * limit is not an error. */
+int it_run_to_steady_state(it_ctx *ctx, int64_t window_steps, double tol, int64_t max_steps,
+                           it_steady_t *out);
 
 /* Synchronise and return all tallies (FP64, reduced in a fixed order so that
  * reruns are bitwise identical). */
@@ -295,9 +313,10 @@ int it_ladder_dt(const it_params *p, double dx_cm, double dt_s, double n_max, do
 int it_dt_log(it_ctx *ctx, int64_t cap, int64_t *first_step, double *dt, double *n_max, int64_t *count);
 
 /* Return the context to its freshly created state without reallocating:
- * densities zero, all tallies zero, step counter and time 0, schedule
- * cleared; the current dt stays and the time-step log restarts from it.
- * Asynchronous on the context stream (no host synchronisation). */
+ * densities zero, all tallies zero, the device error flag cleared (after
+ * IT_ETIMEOUT the context is usable again), step counter and time 0,
+ * schedule cleared; the current dt stays and the time-step log restarts from
+ * it.  Asynchronous on the context stream (no host synchronisation). */
 int it_reset(it_ctx *ctx);
 
 /* Device pointers of the current n+ and n- fields (valid until the next
@@ -483,6 +502,25 @@ int it_step_noalloc(it_grid g, double dx_cm, double dt_s, const it_params *p,
                     const float *dev_plus, const float *dev_minus,
                     float *dev_out_plus, float *dev_out_minus,
                     double *dev_tallies7, void *stream);
+
+/* How long (SM clock cycles) a ring wait of the z-march step kernel may
+ * take before it is declared lost; 0 restores the default of 2^32 cycles
+ * (about 2 s at 2 GHz).  A lost wait ends the launch early: the kernel waits
+ * (always with the full 2^32-cycle bound) for the copies it has issued,
+ * skips its tallies and raises the context's device error flag, which the
+ * next it_tallies reports as IT_ETIMEOUT; it_reset clears it.  A caller
+ * that must notice a stalled device quickly sets a shorter limit; a limit
+ * shorter than a plane's load time makes normal steps fail.  The paper has
+ * no counterpart.  IT_EINVAL for cycles < 0. */
+int it_set_wait_limit(it_ctx *ctx, int64_t cycles);
+
+/* Test hook for the bounded-wait path: with on = 1 the z-march kernel never
+ * issues the first load of its plane ring, so the first wait of every warp
+ * runs out after the it_set_wait_limit limit, without any fault: the
+ * kernel drains the loads it did issue and returns, and IT_ETIMEOUT
+ * follows as described there.  on = 0 restores normal steps.  IT_ESTATE if
+ * the context does not run the z-march kernel (IT_KERNEL_ZMARCH). */
+int it_test_withhold_load(it_ctx *ctx, int on);
 
 /* Destroy a context; NULL is a no-op.  Synchronises the stream first. */
 int it_destroy(it_ctx *ctx);

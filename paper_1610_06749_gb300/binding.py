@@ -60,6 +60,12 @@ class it_sim_desc(ctypes.Structure):
                 ("n_peak_cm3", ctypes.c_double)]
 
 
+class it_steady_t(ctypes.Structure):
+    _fields_ = [("f_ss", ctypes.c_double), ("f_ss_stderr", ctypes.c_double), ("f_window", ctypes.c_double),
+                ("departed", ctypes.c_double), ("released", ctypes.c_double), ("windows", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("stop", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -91,7 +97,7 @@ def lib():
             "it_schedule_tracks": (I, [P, I64, DP, DP, DP, I64P]),
             "it_step": (I, [P, I64]),
             "it_run_to_completion": (I, [P, D, I64, I64, I64P]),
-            "it_run_to_steady_state": (I, [P, I64, D, I64, DP, ctypes.POINTER(I), I64P]),
+            "it_run_to_steady_state": (I, [P, I64, D, I64, ctypes.POINTER(it_steady_t)]),
             "it_tallies": (I, [P, ctypes.POINTER(it_tallies_t)]),
             "it_get_density": (I, [P, I, P, SZ]),
             "it_set_density": (I, [P, P, P, SZ]),
@@ -105,6 +111,8 @@ def lib():
             "it_autotune": (I, [P, I, I, DP]),
             "it_get_launch": (I, [P, IP, IP, IP, IP, IP]),
             "it_step_noalloc": (I, [it_grid, D, D, ctypes.POINTER(it_params), P, P, P, P, P, P]),
+            "it_set_wait_limit": (I, [P, I64]),
+            "it_test_withhold_load": (I, [P, I]),
             "it_batch_create": (I, [ctypes.c_int32, ctypes.POINTER(it_sim_desc), ctypes.POINTER(it_params),
                                     ctypes.POINTER(P)]),
             "it_batch_deposit_tracks": (I, [P, ctypes.c_int32, I64, DP, DP, DP]),
@@ -245,14 +253,12 @@ def it_run_to_completion(h, tol=1e-6, max_steps=10_000_000, check_every=64) -> i
     return done.value
 
 
-def it_run_to_steady_state(h, window_steps=1000, tol=1e-5, max_steps=10_000_000):
-    """Returns (f_ss of the last window, stop: 0 steady / 1 step limit, steps taken)."""
-    f = ctypes.c_double()
-    stop = ctypes.c_int()
-    done = ctypes.c_int64()
-    _check(lib().it_run_to_steady_state(h, int(window_steps), float(tol), int(max_steps), ctypes.byref(f),
-                                        ctypes.byref(stop), ctypes.byref(done)))
-    return f.value, stop.value, done.value
+def it_run_to_steady_state(h, window_steps=1000, tol=1e-5, max_steps=10_000_000) -> dict:
+    """Returns the it_steady_t fields as a dict (f_ss, f_ss_stderr, f_window,
+    departed, released, windows, steps, stop: 0 steady / 1 step limit)."""
+    out = it_steady_t()
+    _check(lib().it_run_to_steady_state(h, int(window_steps), float(tol), int(max_steps), ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in it_steady_t._fields_ if k != "pad_"}
 
 
 def it_tallies(h) -> it_tallies_t:
@@ -329,6 +335,14 @@ def it_step_noalloc(nx, ny, nz, dx_cm, dt_s, p: it_params, dev_plus: int, dev_mi
                                  ctypes.c_void_p(dev_plus), ctypes.c_void_p(dev_minus),
                                  ctypes.c_void_p(dev_out_plus), ctypes.c_void_p(dev_out_minus),
                                  ctypes.c_void_p(dev_tallies7), ctypes.c_void_p(stream)))
+
+
+def it_set_wait_limit(h, cycles: int):
+    _check(lib().it_set_wait_limit(h, int(cycles)))
+
+
+def it_test_withhold_load(h, on: bool):
+    _check(lib().it_test_withhold_load(h, 1 if on else 0))
 
 
 def it_destroy(h):

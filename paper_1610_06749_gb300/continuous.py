@@ -3,19 +3,17 @@
 The 512 x 512 x 256 chamber section (dx = 8 um, gap 2.048 mm, 300 V, FP32,
 periodic lateral faces) under Poisson arrivals of a 20 / 200 keV/um track
 mixture (70 / 30 %, b = 10 um) at the given rates per cm^2 and second
-(Sec. Implementation).  After a warm-up of two ion transit times
-each run continues with it_run_to_steady_state: windows of 1000 steps until
-the efficiency of the ions that left the domain is stable to 1e-5 between
-windows, or ten transit times in all.  Reported: the last window's
-efficiency, what stopped the run, and the efficiency of all ions that left
-the domain after the warm-up (dCol / (dCol + 2 dRec + dLost)).  With tens of
-tracks of a 20 / 200 keV/um mixture per window the window value fluctuates
-by far more than 1e-5, so the step limit usually ends the run; with almost
-no recombination in two windows in a row (sparse arrivals) the rule is met
-trivially at f = 1.  Upwind drift:
-at the recombination-bound time step Lax-Wendroff's undershoots turn the
-recombination term into a source.  Every step runs in the CUDA solver; this
-module only generates the arrivals (synth) and reports.
+(Sec. Implementation, "Distribution of ion tracks").  After a warm-up of two
+ion transit times each run continues with it_run_to_steady_state: windows of
+1000 steps until the departure efficiency of every ion that has left the
+domain since the warm-up, Col / (Col + 2 Rec + Lost), moves by less than
+1e-5 over a window that carried departures, or the step limit (a number of
+transit times).  Reported: that efficiency with its batch-means standard
+error, what stopped the run, the last window's own efficiency and the
+cumulative f.  Upwind drift: at the recombination-bound time step
+Lax-Wendroff's undershoots turn the recombination term into a source.
+Every step runs in the CUDA solver; this module only generates the arrivals
+(synth) and reports.
 
     python -m paper_1610_06749_gb300.continuous [rate ...]
 """
@@ -31,7 +29,7 @@ from . import binding as B
 from . import synth
 
 
-def run(rate_per_cm2_s: float, window: int = 1000, tol: float = 1e-5, transits: float = 10.0) -> dict:
+def run(rate_per_cm2_s: float, window: int = 1000, tol: float = 1e-5, transits: float = 100.0) -> dict:
     w = synth.continuous_512x512x256()
     npk = B.it_peak_density([200.0], [w.b_cm])
     with B.Simulation(w.nx, w.ny, w.nz, w.dx_cm, w.voltage_V, n_peak_cm3=npk, scheme=B.IT_UPWIND) as sim:
@@ -47,18 +45,16 @@ def run(rate_per_cm2_s: float, window: int = 1000, tol: float = 1e-5, transits: 
         warm = (2 * transit_steps + window - 1) // window * window
         t0 = time.perf_counter()
         sim.step(warm)
-        tw = sim.tallies()
-        f_ss, stop, steps = sim.run_to_steady_state(window_steps=window, tol=tol, max_steps=max_steps - warm)
+        r = sim.run_to_steady_state(window_steps=window, tol=tol, max_steps=max_steps - warm)
         el = time.perf_counter() - t0
         t = sim.tallies()
-        dc = t.collected.sum() - tw.collected.sum()
-        gone = dc + 2.0 * (t.recombined - tw.recombined) + (t.lost_lateral.sum() - tw.lost_lateral.sum())
-        steps += warm
+        steps = warm + r["steps"]
         return {"workload": w.name, "rate_per_cm2_s": rate_per_cm2_s, "tracks_scheduled": len(tr),
-                "dt_s": dt, "transit_steps": transit_steps, "window_steps": window, "tol": tol,
-                "f_ss": f_ss, "stopped_by": "steady state" if stop == 0 else "step limit (10 transits)",
-                "steps": steps, "warmup_steps": warm, "seconds": el, "f_after_warmup": dc / gone if gone else None,
-                "f_cumulative": t.f,
+                "tracks_arrived": int(np.sum(tr.step < steps)), "dt_s": dt, "transit_steps": transit_steps,
+                "window_steps": window, "tol": tol, "f_ss": r["f_ss"], "f_ss_stderr": r["f_ss_stderr"],
+                "f_last_window": r["f_window"], "windows": r["windows"],
+                "stopped_by": "steady state" if r["stop"] == 0 else f"step limit ({transits:g} transits)",
+                "steps": steps, "warmup_steps": warm, "seconds": el, "f_cumulative": t.f,
                 "cell_updates_per_s": w.cells * steps / el, "launch": sim.launch()}
 
 

@@ -103,19 +103,35 @@ static void make_coef(Coef<T> &cf, const it_params *p, double dx, double dt) {
             wzp = sd + 0.5 * c * c - 0.5 * sigma * c;
         }
         double wx = sd, wy = sd;
-        double w0 = 1.0 - (2.0 * wx + 2.0 * wy + wzm + wzp);
+        // increment form of the update, n' = n + [wc n + wx (l + r) + wy (u + d)
+        // + wzm n_{k-1} + wzp n_{k+1} - alpha dt n+ n-]: the centre weight
+        // enters as wc = w0 - 1 = -(2 wx + 2 wy + wzm + wzp), so the five
+        // transport weights of the bracket sum to zero
+        double wc = -(2.0 * wx + 2.0 * wy + wzm + wzp);
         if (sizeof(T) == 4) {
-            // common grid q = ulp_f32(w0) (w0 >= 2^-20 assumed for the grid; smaller
-            // w0 uses 2^-43) so that 1 - sum is exact and representable in FP32
-            const int e0 = w0 > 0 ? std::max(std::ilogb(w0), -20) : -20;
-            const double q = std::ldexp(1.0, e0 - 23);
-            wx = round_to_grid(wx, q, 24);
-            wy = round_to_grid(wy, q, 24);
-            wzm = round_to_grid(wzm, q, 24);
-            wzp = round_to_grid(wzp, q, 24);
-            w0 = 1.0 - (2.0 * wx + 2.0 * wy + wzm + wzp);   // exact in FP64
+            // one common grid q for the FP32 weights, a power of two at 2^-23
+            // of the largest weight: every weight is a multiple of q, so the sum
+            // that gives wc is exact in FP64, and every weight (wc included)
+            // stays below 2^24 q and is exact in FP32.  The bracket's weights
+            // then sum to zero exactly and charge is conserved in real
+            // arithmetic; the grid is 2^-23 of the largest weight (~0.06 at the
+            // workloads' steps), not 2^-23 of w0 ~ 1, so the weights carry 16x
+            // less rounding than a grid set by w0.
+            const double big = std::max({std::fabs(wc), std::fabs(wx), std::fabs(wzm), std::fabs(wzp)});
+            int e = big > 0 ? std::max(std::ilogb(big), -100) : -100;
+            for (;;) {
+                const double q = std::ldexp(1.0, e - 23), lim = std::ldexp(1.0, e + 1);
+                const double rx = round_to_grid(wx, q, 24), ry = round_to_grid(wy, q, 24);
+                const double rzm = round_to_grid(wzm, q, 24), rzp = round_to_grid(wzp, q, 24);
+                const double rc = -(2.0 * rx + 2.0 * ry + rzm + rzp);   // exact in FP64
+                if (std::fabs(rc) < lim && std::fabs(rx) < lim && std::fabs(rzm) < lim && std::fabs(rzp) < lim) {
+                    wx = rx; wy = ry; wzm = rzm; wzp = rzp; wc = rc;
+                    break;
+                }
+                ++e;
+            }
         }
-        cf.w0[s] = (T)w0;
+        cf.wc[s] = (T)wc;
         cf.wx[s] = (T)wx;
         cf.wy[s] = (T)wy;
         cf.wzm[s] = (T)wzm;
@@ -704,22 +720,25 @@ int it_run_to_completion(it_ctx *c, double tol, int64_t max_steps, int64_t check
     return rc;
 }
 
-int it_run_to_steady_state(it_ctx *c, int64_t window_steps, double tol, int64_t max_steps, double *f_ss, int *stop,
-                           int64_t *steps_done) {
+int it_run_to_steady_state(it_ctx *c, int64_t window_steps, double tol, int64_t max_steps, it_steady_t *out) {
     if (!c) return fail(IT_EINVAL, "ctx is NULL");
     if (window_steps < 1 || !(tol >= 0) || max_steps < 0) return fail(IT_EINVAL, "bad argument");
     const int64_t start = c->steps;
     it_tallies_t t;
     int rc = it_tallies(c, &t);
-    // ions that have left the domain so far, by route
+    // ions that have left the domain so far, by route, and ions released
     auto col = [](const it_tallies_t &x) {
         return x.collected_anode[0] + x.collected_anode[1] + x.collected_cathode[0] + x.collected_cathode[1];
     };
     auto lost = [](const it_tallies_t &x) { return x.lost_lateral[0] + x.lost_lateral[1]; };
-    double c0 = col(t), r0 = t.recombined, l0 = lost(t);
-    double f_prev = std::nan(""), f_cur = std::nan("");
+    auto rel = [](const it_tallies_t &x) { return x.released[0] + x.released[1]; };
+    const double c_start = col(t), r_start = t.recombined, l_start = lost(t), rel_start = rel(t);
+    double c0 = c_start, r0 = r_start, l0 = l_start;
+    // per-window collected and departed ions, for the batch-means error
+    std::vector<double> wc, wg;
+    double F_prev = std::nan(""), F = std::nan(""), f_win = std::nan("");
+    double C = 0.0, G = 0.0, Rel = 0.0;
     int code = 1;
-    int64_t windows = 0;
     while (rc == IT_OK && c->steps - start + window_steps <= max_steps) {
         rc = it_step(c, window_steps);
         if (rc) break;
@@ -728,18 +747,52 @@ int it_run_to_steady_state(it_ctx *c, int64_t window_steps, double tol, int64_t 
         if (!std::isfinite(t.in_domain[0] + t.in_domain[1] + t.recombined)) { rc = fail(IT_EUNSTABLE, "state is not finite"); break; }
         const double dc = col(t) - c0, dr = t.recombined - r0, dl = lost(t) - l0;
         c0 = col(t); r0 = t.recombined; l0 = lost(t);
-        const double gone = dc + 2.0 * dr + dl;   // a recombined pair removes two ions
-        f_cur = gone != 0.0 ? dc / gone : std::nan("");
-        ++windows;
-        if (windows >= 2 && std::isfinite(f_cur) && std::isfinite(f_prev) && std::fabs(f_cur - f_prev) < tol) {
+        const double g = dc + 2.0 * dr + dl;   // a recombined pair removes two ions
+        wc.push_back(dc);
+        wg.push_back(g);
+        f_win = g != 0.0 ? dc / g : std::nan("");
+        // aggregate since the call began (sums of the cumulative tallies'
+        // differences, so no window's rounding is lost)
+        C = col(t) - c_start;
+        G = C + 2.0 * (t.recombined - r_start) + (lost(t) - l_start);
+        Rel = rel(t) - rel_start;
+        F = G != 0.0 ? C / G : std::nan("");
+        const double n = (double)wc.size();
+        // a window is judged only when it carried departures of at least half
+        // the mean release per window, and the aggregate at least half of
+        // everything released since the call began
+        const bool judged = g > 0.0 && g >= 0.5 * Rel / n && G >= 0.5 * Rel;
+        if (judged && wc.size() >= 2 && std::isfinite(F) && std::isfinite(F_prev) && std::fabs(F - F_prev) < tol) {
             code = 0;
             break;
         }
-        f_prev = f_cur;
+        F_prev = F;
     }
-    if (f_ss) *f_ss = f_cur;
-    if (stop) *stop = code;
-    if (steps_done) *steps_done = c->steps - start;
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->f_ss = F;
+        out->f_window = f_win;
+        out->departed = G;
+        out->released = Rel;
+        out->windows = (int64_t)wc.size();
+        out->steps = c->steps - start;
+        out->stop = code;
+        // ratio estimator C/G with batch means over nb contiguous batches of windows
+        const int64_t n = (int64_t)wc.size();
+        const int64_t nb = n >= 10 ? 10 : 0;
+        double se = std::nan("");
+        if (nb >= 2 && G != 0.0 && std::isfinite(F)) {
+            double ss = 0.0;
+            for (int64_t b = 0; b < nb; ++b) {
+                double cb = 0.0, gb = 0.0;
+                for (int64_t w = b * n / nb; w < (b + 1) * n / nb; ++w) { cb += wc[w]; gb += wg[w]; }
+                const double e = cb - F * gb;
+                ss += e * e;
+            }
+            se = std::sqrt(ss * (double)nb / (double)(nb - 1)) / G;
+        }
+        out->f_ss_stderr = se;
+    }
     return rc;
 }
 
@@ -805,6 +858,7 @@ int it_reset(it_ctx *c) {
     IT_CK(cudaMemsetAsync(c->n[c->cur][1], 0, bytes, c->stream));
     IT_CK(cudaMemsetAsync(c->d_slots, 0, sizeof(double) * NT * c->nslots, c->stream));
     IT_CK(cudaMemsetAsync(c->d_acc, 0, sizeof(DevAcc), c->stream));
+    IT_CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     c->steps = 0;
     c->t_s = 0.0;
     c->sched_step.clear(); c->sched_tr.clear(); c->sched_ptr = 0;
@@ -855,6 +909,24 @@ int it_get_launch(it_ctx *c, int *kernel, int *tile_rows, int *ctas_per_sm, int 
     if (ctas_per_sm) *ctas_per_sm = zm ? c->zm.ctas_per_sm : zm2 ? c->zm2.ctas_per_sm : 0;
     if (stages) *stages = zm ? c->zm.S : zm2 ? c->zm2.S : 0;
     if (ctas) *ctas = zm2 ? c->zm2.grid : c->nslots;
+    return IT_OK;
+}
+
+int it_set_wait_limit(it_ctx *c, int64_t cycles) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (cycles < 0) return fail(IT_EINVAL, "cycles must be >= 0");
+    c->wait_cycles = cycles;
+    // a captured segment holds the old kernel arguments
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return IT_OK;
+}
+
+int it_test_withhold_load(it_ctx *c, int on) {
+    if (!c) return fail(IT_EINVAL, "ctx is NULL");
+    if (on != 0 && on != 1) return fail(IT_EINVAL, "on must be 0 or 1");
+    if (on && c->kernel != IT_KERNEL_ZMARCH) return fail(IT_ESTATE, "the test hook applies to the z-march kernel only");
+    c->withhold = on;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     return IT_OK;
 }
 

@@ -88,7 +88,7 @@ step_batched_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restr
                     const float zm = (k > 0) ? in[idx - plane] : 0.f;
                     const float zp = (k < nz - 1) ? in[idx + plane] : 0.f;
                     float v =
-                        upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.w0[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
+                        upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.wc[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
                     if constexpr (SC) {
                         v = add_sc(v, c.sc[s], n0, p0, m0);
                         acc[NQ - 2 + s] += (double)__fmul_rn(n0, __fsub_rn(p0, m0));
@@ -206,7 +206,7 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
             float r = __shfl_down_sync(0xffffffffu, n.x, 1);
             if (need_l) l = zero_l ? 0.f : __ldg(in_[s] + pk + row_l);
             if (need_r) r = zero_r ? 0.f : __ldg(in_[s] + pk + row_r);
-            float4 v = upd7x4(n, l, r, u, d, prev[s], nxt[s], rxy, rzw, c.w0[s], c.wx[s], c.wy[s], c.wzm[s],
+            float4 v = upd7x4(n, l, r, u, d, prev[s], nxt[s], rxy, rzw, c.wc[s], c.wx[s], c.wy[s], c.wzm[s],
                               c.wzp[s], c.adt);
             if (SC) {
                 float2 pxy, pzw;

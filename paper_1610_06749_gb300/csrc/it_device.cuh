@@ -31,27 +31,33 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *smem /* [32][N
     }
 }
 
-// One cell of the update in the weight form of Coef (the same operation
-// sequence in every kernel, so all kernels round identically).
+// One cell of the update in the increment form of Coef: n + [wc n + wx (l + r)
+// + wy (u + d) + wzm zm + wzp zp - adt rr], the bracket's transport weights
+// summing to zero (wc = w0 - 1).  The bracket's terms are a few percent of n,
+// so their rounding errors are too, and the one rounding of n + bracket is
+// the only one at the scale of n.  The same operation sequence in every
+// kernel, so all kernels round identically.
 __device__ __forceinline__ float upd7(float n, float l, float r, float u, float d, float zm, float zp, float rr,
-                                      float w0, float wx, float wy, float wzm, float wzp, float adt) {
-    float v = w0 * n;
-    v = __fmaf_rn(wx, l + r, v);
-    v = __fmaf_rn(wy, u + d, v);
+                                      float wc, float wx, float wy, float wzm, float wzp, float adt) {
+    float v = __fmul_rn(wc, n);
+    v = __fmaf_rn(wx, __fadd_rn(l, r), v);
+    v = __fmaf_rn(wy, __fadd_rn(u, d), v);
     v = __fmaf_rn(wzm, zm, v);
     v = __fmaf_rn(wzp, zp, v);
-    return __fmaf_rn(-adt, rr, v);
+    v = __fmaf_rn(-adt, rr, v);
+    return __fadd_rn(n, v);
 }
 
 __device__ __forceinline__ double upd7(double n, double l, double r, double u, double d, double zm, double zp,
-                                       double rr, double w0, double wx, double wy, double wzm, double wzp,
+                                       double rr, double wc, double wx, double wy, double wzm, double wzp,
                                        double adt) {
-    double v = w0 * n;
-    v = __fma_rn(wx, l + r, v);
-    v = __fma_rn(wy, u + d, v);
+    double v = __dmul_rn(wc, n);
+    v = __fma_rn(wx, __dadd_rn(l, r), v);
+    v = __fma_rn(wy, __dadd_rn(u, d), v);
     v = __fma_rn(wzm, zm, v);
     v = __fma_rn(wzp, zp, v);
-    return __fma_rn(-adt, rr, v);
+    v = __fma_rn(-adt, rr, v);
+    return __dadd_rn(n, v);
 }
 
 // The space-charge term of one cell, after upd7: v + sc n (n+ - n-), in this

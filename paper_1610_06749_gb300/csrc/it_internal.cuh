@@ -24,16 +24,17 @@ constexpr int NM = 6;
 // finalize output: NT tallies, NM monitor values, released +/-, error flag
 constexpr int NOUT = NT + NM + 3;
 
-// Update weights of one species:
-//   n' = w0 n + wx (x- + x+) + wy (y- + y+) + wzm z- + wzp z+ - adt n+ n-
-// wzm multiplies the neighbour at k-1, wzp the one at k+1.  For FP32 the
-// weights are rounded onto a common grid so that w0 + 2wx + 2wy + wzm + wzp
-// is exactly 1 with every weight exactly representable: the rounded scheme
+// Update weights of one species, in increment form:
+//   n' = n + [wc n + wx (x- + x+) + wy (y- + y+) + wzm z- + wzp z+ - adt n+ n-]
+// with wc = w0 - 1 = -(2wx + 2wy + wzm + wzp); wzm multiplies the neighbour
+// at k-1, wzp the one at k+1.  For FP32 the weights lie on one common grid
+// (2^-23 of the largest weight) so that the bracket's transport weights sum
+// to exactly 0 with every weight exactly representable: the rounded scheme
 // then conserves charge exactly in real arithmetic (only per-operation
-// rounding remains), at a relative perturbation of the weights below 1e-6.
+// rounding remains), at a relative perturbation of the weights below 1e-7.
 template <typename T>
 struct Coef {
-    T w0[2], wx[2], wy[2], wzm[2], wzp[2];
+    T wc[2], wx[2], wy[2], wzm[2], wzp[2];   // wc = w0 - 1: the centre weight of the increment form
     T adt;            // alpha * dt
     T sc[2];          // space charge: the update adds sc[s] n_s (n+ - n-);
                       // sc = -dt mu+ q/eps0 for n+, +dt mu- q/eps0 for n-
@@ -69,6 +70,8 @@ struct ZmConf {
     size_t smem;      // dynamic shared memory per CTA
     int threads;      // 256
     int ctas_per_sm;
+    long long wait_cycles;   // SM cycles a ring wait may take before it is declared lost
+    int withhold;            // test hook: 1 = the first ring load is never issued
 };
 
 // Launch shape of the two-steps-per-launch z-march kernel: tiles of TY
@@ -148,6 +151,8 @@ struct it_ctx {
     itk::Coef<float> cf;
     itk::Coef<double> cd;
     int *d_err;           // device error flag (bounded waits that ran out)
+    long long wait_cycles;   // ring-wait limit of the z-march kernel (it_set_wait_limit)
+    int withhold;            // test hook of it_test_withhold_load
 };
 
 namespace itk {

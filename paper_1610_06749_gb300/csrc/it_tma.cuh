@@ -145,14 +145,15 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
 // and the sequence is the one of upd7, so the results are bitwise those of
 // the scalar kernels.
 __device__ __forceinline__ float4 upd7x4(float4 n, float l, float r, float4 u, float4 d, float4 zm, float4 zp,
-                                         float2 rxy, float2 rzw, float w0, float wx, float wy, float wzm, float wzp,
+                                         float2 rxy, float2 rzw, float wc, float wx, float wy, float wzm, float wzp,
                                          float adt) {
-    const float2 W0 = make_float2(w0, w0), WX = make_float2(wx, wx), WY = make_float2(wy, wy);
+    const float2 WC = make_float2(wc, wc), WX = make_float2(wx, wx), WY = make_float2(wy, wy);
     const float2 WZM = make_float2(wzm, wzm), WZP = make_float2(wzp, wzp), NA = make_float2(-adt, -adt);
-    float2 a = __fmul2_rn(W0, make_float2(n.x, n.y));
-    float2 b = __fmul2_rn(W0, make_float2(n.z, n.w));
-    a = __ffma2_rn(WX, make_float2(l + n.y, n.x + n.z), a);
-    b = __ffma2_rn(WX, make_float2(n.y + n.w, n.z + r), b);
+    const float2 nxy = make_float2(n.x, n.y), nzw = make_float2(n.z, n.w);
+    float2 a = __fmul2_rn(WC, nxy);
+    float2 b = __fmul2_rn(WC, nzw);
+    a = __ffma2_rn(WX, __fadd2_rn(make_float2(l, n.x), make_float2(n.y, n.z)), a);
+    b = __ffma2_rn(WX, __fadd2_rn(make_float2(n.y, n.z), make_float2(n.w, r)), b);
     a = __ffma2_rn(WY, __fadd2_rn(make_float2(u.x, u.y), make_float2(d.x, d.y)), a);
     b = __ffma2_rn(WY, __fadd2_rn(make_float2(u.z, u.w), make_float2(d.z, d.w)), b);
     a = __ffma2_rn(WZM, make_float2(zm.x, zm.y), a);
@@ -161,6 +162,8 @@ __device__ __forceinline__ float4 upd7x4(float4 n, float l, float r, float4 u, f
     b = __ffma2_rn(WZP, make_float2(zp.z, zp.w), b);
     a = __ffma2_rn(NA, rxy, a);
     b = __ffma2_rn(NA, rzw, b);
+    a = __fadd2_rn(nxy, a);
+    b = __fadd2_rn(nzw, b);
     return make_float4(a.x, a.y, b.x, b.y);
 }
 

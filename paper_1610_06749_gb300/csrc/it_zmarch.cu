@@ -22,9 +22,11 @@
 //   * results are stored with coalesced 16-byte stores; per-thread FP32
 //     partial sums (at most 32 planes) are reduced per warp in FP64 and per
 //     CTA into the CTA's own tally slot (deterministic).
-// Every mbarrier wait is bounded: a wait that runs out raises the device
-// error flag, and the CTA waits (bounded) for its outstanding copies and
-// returns.
+// Every mbarrier wait is bounded: a ring wait that runs out (after
+// zc.wait_cycles SM cycles, 2^32 by default) raises the device error flag,
+// and the CTA waits, with the full 2^32-cycle bound, for the copies it has
+// issued and returns.  A test hook (zc.withhold) leaves the first ring load
+// unissued, so that every warp's first wait runs out without any fault.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -127,7 +129,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         for (int q = 0; q < NW * WQ; ++q) wacc[q] = 0.0;
         abort_flag = 0;
         fence_mbar_init();
-        for (int n = 0; n < S && n < nload; ++n) issue(n);
+        for (int n = zc.withhold ? 1 : 0; n < S && n < nload; ++n) issue(n);
     }
     __syncthreads();
 
@@ -170,7 +172,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     int nrel = 0;            // planes of the sequence this warp has released
     bool failed = false;
 
-    // Wait (bounded, about 2^32 cycles) for the plane at ring position u.  A
+    // Wait (bounded by zc.wait_cycles) for the plane at ring position u.  A
     // lost wait marks the whole warp failed (shuffles stay convergent) and
     // raises the CTA's abort flag, after which no warp waits again.
     auto wait_full = [&](const RingPos &u) {
@@ -181,7 +183,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         for (;;) {
             ok = ok || mbar_try_wait(&full[u.slot], u.phase);
             if (__all_sync(0xffffffffu, ok)) return;
-            if (__any_sync(0xffffffffu, abort_flag || clock64() - t0 > (1LL << 32))) break;
+            if (__any_sync(0xffffffffu, abort_flag || clock64() - t0 > zc.wait_cycles)) break;
         }
         failed = true;
         if (lane == 0) abort_flag = 1;
@@ -264,7 +266,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                         if (c4_[it] == 0) l = 0.f;
                         if (c4_[it] == ncol4 - 1) r = 0.f;
                     }
-                    float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw, cf.w0[s], cf.wx[s], cf.wy[s],
+                    float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw, cf.wc[s], cf.wx[s], cf.wy[s],
                                       cf.wzm[s], cf.wzp[s], cf.adt);
                     if (SC) {
                         float2 pxy, pzw;
@@ -517,7 +519,9 @@ int launch_step_zmarch(it_ctx *c, cudaStream_t s) {
     maps.halo[0] = c->tm_halo[cur][0];
     maps.halo[1] = c->tm_halo[cur][1];
     float *op = (float *)c->n[nxt][0], *om = (float *)c->n[nxt][1];
-    const ZmConf &z = c->zm;
+    ZmConf z = c->zm;
+    z.wait_cycles = c->wait_cycles > 0 ? c->wait_cycles : (1LL << 32);
+    z.withhold = c->withhold;
     const bool per = c->p.lateral_bc == IT_PERIODIC;
     const int nw = z.threads / 32;
     const int ipt = ipt_of(c, z.TY, nw);

@@ -98,6 +98,9 @@ int main(void) {
     S(it_sim_desc) F(it_sim_desc, nx) F(it_sim_desc, ny) F(it_sim_desc, nz) F(it_sim_desc, dx_cm)
     F(it_sim_desc, dt_s) F(it_sim_desc, voltage_V) F(it_sim_desc, n_peak_cm3)
     S(it_grid)
+    S(it_steady_t) F(it_steady_t, f_ss) F(it_steady_t, f_ss_stderr) F(it_steady_t, f_window)
+    F(it_steady_t, departed) F(it_steady_t, released) F(it_steady_t, windows) F(it_steady_t, steps)
+    F(it_steady_t, stop)
     return 0;
 }
 """
@@ -121,7 +124,7 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         got = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
         assert got == int(val), (tname, field, got, val)
         seen += 1
-    assert seen == 39
+    assert seen == 48
 
 
 def test_peak_density_and_state_bytes(L):

@@ -42,7 +42,11 @@ def test_forward_matches_reference():
         mean, spread, per = B.it_mlp_predict(h, MEMBERS, X)
         for m in range(MEMBERS):
             ref, _ = M.forward(theta[m], X, quant=True)
-            assert np.max(np.abs(per[:, m] - ref)) < 2e-3
+            # measured: <= 3e-6; the members' FP32 tensor-core sums and the
+            # reference's FP64 sums round the same bf16 points differently
+            # only where a value sits on a rounding boundary
+            print(f"forward member {m}: max abs {np.max(np.abs(per[:, m] - ref)):.3e}")
+            assert np.max(np.abs(per[:, m] - ref)) < 1e-4
         assert np.allclose(mean, per.mean(axis=1)) and np.allclose(spread, per.max(axis=1) - per.min(axis=1))
     finally:
         B.it_mlp_destroy(h)
@@ -56,11 +60,14 @@ def test_gradients_match_reference():
         offs = np.cumsum([0] + [int(np.prod(s)) for s in M.SHAPES])
         for m in range(MEMBERS):
             lref, gref = M.loss_and_grad(theta[m], X, y, quant=True)
-            assert loss[m] == pytest.approx(lref, rel=2e-3)
+            print(f"loss member {m}: {loss[m]:.9e} vs {lref:.9e}")
+            assert loss[m] == pytest.approx(lref, rel=1e-4)
             for t in range(len(M.SHAPES)):
                 a, b = g[m, offs[t]:offs[t + 1]].astype(np.float64), gref[offs[t]:offs[t + 1]]
                 err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-                assert err < 2e-2, (m, t, err)
+                print(f"grad member {m} tensor {t}: normwise {err:.3e}")
+                # measured: <= 2.6e-4 per tensor
+                assert err < 1e-3, (m, t, err)
     finally:
         B.it_mlp_destroy(h)
 

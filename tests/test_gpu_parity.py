@@ -2,13 +2,17 @@
 
 Densities (FP32 storage): max|n_gpu - n_orc| / max|n_orc| <= 1e-4 per
 species (the normwise reading of "1e-4 max relative error"), and pointwise
-relative error <= 1e-4 wherever |n_orc| >= 5e-2 max.  Closer to zero the
-pointwise relative error of any FP32 evaluation of the scheme grows with the
-cancellation in the Lax-Wendroff oscillations (a float32 numpy restatement
-of the update reaches 2.6e-4 at 1e-3 max after 75 steps), so it is not a
-correctness signal there.  FP64 storage: 1e-12.  f within 1e-5 absolute
-(FP32) or 1e-12 (FP64).  Sizes span several tiles and ragged tails; the
-full-size workloads run in the launch configuration the benchmark times.
+relative error <= 1e-4 on the cells at or above 1e-3 of the maximum for
+upwind drift, and at or above 5e-2 of the maximum for Lax-Wendroff drift.
+Lax-Wendroff's negative downstream weight makes a small cell next to a steep
+front the difference of large neighbour terms, so FP32 rounding there is
+relative to the neighbours: a plain float32 evaluation of the same update
+exceeds 1e-4 at 1e-3 of the maximum after 75 steps (tests/test_fp32_rounding.py,
+no GPU), while upwind's convex weights keep it relative to the cell.  FP64
+storage: 1e-12.  f within 1e-5 absolute (FP32) or 1e-12 (FP64).  Sizes span
+several tiles and ragged tails; the full-size workloads run in the launch
+configuration the benchmark times; the long-horizon cases compare the full
+arrays at steps 1, 10, 100, 1000 and at the end of the run.
 """
 import numpy as np
 import pytest
@@ -111,7 +115,8 @@ def test_small_grids_match_oracle(case):
             O.step(chk - done)
             done = chk
             for s in range(2):
-                assert_density_close(g.density(s), O.density(s), 1e-4, what=f"step {chk} species {s}")
+                assert_density_close(g.density(s), O.density(s), 1e-4, core=1e-3 if sch == B.IT_UPWIND else 5e-2,
+                                     what=f"step {chk} species {s}")
         compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
 
 
@@ -388,10 +393,14 @@ def test_steady_state_runner_matches_oracle():
     g, O = make_pair(nx, ny, nz, dx, V, tr, scheme=B.IT_UPWIND, dt=dt)
     with g:
         g.schedule(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step)
-        fg, sg, ng = g.run_to_steady_state(window_steps=50, tol=2e-3, max_steps=1500)
-        fo, so, no = O.run_to_steady_state(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step, 50, 2e-3, 1500)
-        assert (sg, ng) == (so, no)
-        assert fg == pytest.approx(fo, abs=1e-5)
+        rg = g.run_to_steady_state(window_steps=50, tol=2e-4, max_steps=1500)
+        ro = O.run_to_steady_state(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm, tr.step, 50, 2e-4, 1500)
+        print(f"steady state: GPU {rg} oracle {ro}")
+        assert (rg["stop"], rg["steps"], rg["windows"]) == (ro["stop"], ro["steps"], ro["windows"])
+        for k in ("f_ss", "f_window", "f_ss_stderr"):
+            assert rg[k] == pytest.approx(ro[k], abs=1e-5, nan_ok=True), k
+        assert rg["departed"] == pytest.approx(ro["departed"], rel=1e-5)
+        assert rg["released"] == pytest.approx(ro["released"], rel=1e-6)
         compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
 
 
@@ -408,9 +417,121 @@ def test_steady_state_of_a_sparse_track_train_is_the_single_track_f_on_gpu():
         f1 = one.tallies().f
         steps = np.arange(n, dtype=np.int64) * P
         train.schedule(np.full(n, 0.5 * nx * dx), np.full(n, 0.5 * ny * dx), np.full(n, let), np.full(n, b), steps)
-        f_ss, stop, done = train.run_to_steady_state(window_steps=P, tol=1e-7, max_steps=n * P)
-        assert stop == 0 and done == 2 * P
-        # the window sums are differences of cumulative FP64 tallies built
-        # from FP32 partials (1e-8 level); a miscounted route of the ions that
-        # left would be off by O(0.1)
-        assert f_ss == pytest.approx(f1, abs=1e-6)
+        r = train.run_to_steady_state(window_steps=P, tol=1e-7, max_steps=n * P)
+        assert r["stop"] == 0 and r["steps"] == 2 * P and r["windows"] == 2
+        # the sums are differences of cumulative FP64 tallies built from FP32
+        # partials (1e-8 level); a miscounted route of the ions that left
+        # would be off by O(0.1)
+        assert r["f_ss"] == pytest.approx(f1, abs=1e-6)
+        assert r["f_window"] == pytest.approx(f1, abs=1e-6)
+
+
+def density_errors(gpu, orc, floor=0.0):
+    """Normwise error max|dn| / max|n| and the largest pointwise relative
+    error on the cells at or above 1e-3, 1e-2 and 5e-2 of the maximum."""
+    scale = max(np.max(np.abs(orc)), floor)
+    diff = np.abs(gpu.astype(np.float64) - orc)
+    out = {"norm": float(np.max(diff) / scale)}
+    for core in (1e-3, 1e-2, 5e-2):
+        big = np.abs(orc) >= core * scale
+        out[core] = float(np.max(diff[big] / np.abs(orc[big]))) if big.any() else 0.0
+    return out
+
+
+# Long-horizon parity (density checkpoints at steps 1, 10, 100 and 1000) on a
+# grid that takes the z-march's multi-tile, multi-segment paths: 128 x 128 x
+# 200 cells at dx = 5 um with 500 tracks, the track density of the pulsed
+# 256 x 256 x 400 workload, LET log-uniform 1-1000 keV/um.  Upwind runs at
+# 200 V.  Lax-Wendroff runs at 400 V: at 200 V its undershoots next to the
+# densest tracks turn the recombination term into a source at the
+# recombination-bound step and the state grows (n_max x 3 by step 1000 in
+# the FP64 oracle); at 400 V the Courant number is twice as large and the
+# scheme stays bounded.  Pointwise checks as in the module docstring
+# (measured at step 1000: upwind 5e-6 at 1e-3 of the maximum; Lax-Wendroff
+# 1.4e-5 at 5e-2 of the maximum and 3.6e-4 at 1e-3).
+LONG_CASES = [
+    (B.IT_LAX_WENDROFF, B.IT_PERIODIC, 400.0),
+    (B.IT_LAX_WENDROFF, B.IT_ABSORBING, 400.0),
+    (B.IT_UPWIND, B.IT_PERIODIC, 200.0),
+    (B.IT_UPWIND, B.IT_ABSORBING, 200.0),
+]
+
+
+@pytest.mark.parametrize("case", LONG_CASES, ids=lambda c: f"s{c[0]}-bc{c[1]}-{int(c[2])}V")
+def test_long_horizon_checkpoints_128x128x200(case):
+    sch, lat, V = case
+    nx, ny, nz, dx = 128, 128, 200, 5e-4
+    tr = synth.uniform_tracks(1610067500, 500, nx * dx, ny * dx, 1e-3, let="loguniform")
+    g, O = make_pair(nx, ny, nz, dx, V, tr, lateral=lat, scheme=sch)
+    core = 1e-3 if sch == B.IT_UPWIND else 5e-2
+    with g:
+        assert g.launch()["kernel"] == B.IT_KERNEL_ZMARCH
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        done = 0
+        for chk in (1, 10, 100, 1000):
+            g.step(chk - done)
+            O.step(chk - done)
+            done = chk
+            for s in range(2):
+                gd, od = g.density(s), O.density(s)
+                print(f"long {case} step {chk} species {s}: {density_errors(gd, od)}")
+                assert_density_close(gd, od, 1e-4, core=core, what=f"step {chk} species {s}")
+            compare_tallies(g.tallies(), O.tallies(), 1e-5, 1e-5)
+
+
+@pytest.mark.parametrize("case", [(B.IT_LAX_WENDROFF, B.IT_PERIODIC, 400.0), (B.IT_UPWIND, B.IT_ABSORBING, 200.0)],
+                         ids=lambda c: f"s{c[0]}-bc{c[1]}-{int(c[2])}V")
+def test_run_to_the_end_64x48x200(case):
+    # the last checkpoint, min(1e4 steps, completion): the GPU runs to
+    # completion (in-domain / released < 1e-6, checked every 64 steps) and the
+    # oracle takes the same number of steps.  What is left then is a tail far
+    # below the deposited peak, so densities are measured against 1e-4 of
+    # the deposited maximum; f must agree to 1e-5 at the end of the run.
+    sch, lat, V = case
+    nx, ny, nz, dx = 64, 48, 200, 5e-4
+    tr = synth.uniform_tracks(1610067501, 94, nx * dx, ny * dx, 1e-3, let="loguniform")
+    g, O = make_pair(nx, ny, nz, dx, V, tr, lateral=lat, scheme=sch)
+    with g:
+        g.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        O.deposit(tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        peak = max(np.max(O.density(0)), np.max(O.density(1)))
+        steps = g.run_to_completion(tol=1e-6, max_steps=10_000, check_every=64)
+        O.step(steps)
+        tg, to = g.tallies(), O.tallies()
+        print(f"end {case}: steps {steps} f {tg.f:.8f} vs {to.f:.8f} in-domain {tg.in_domain.sum() / tg.released.sum():.2e}")
+        for s in range(2):
+            gd, od = g.density(s), O.density(s)
+            print(f"end {case} species {s}: {density_errors(gd, od, floor=1e-4 * peak)}")
+            assert_density_close(gd, od, 1e-4, core=1e-3 if sch == B.IT_UPWIND else 5e-2,
+                                 what=f"end species {s}", floor=1e-4 * peak)
+        compare_tallies(tg, to, 1e-5, 1e-5)
+
+
+def test_single_track_dx_sweep_fp64_matches_oracle_and_records_the_jaffe_gap():
+    # The single-track workload at dx = b/5, b/10, b/20 (48^2 x 100 up to
+    # 192^2 x 400 cells), FP64 on the GPU, run to completion with the
+    # oracle's rule.  Each f equals the FP64 oracle's (tests/golden/
+    # single_track_dx_sweep.json, written by the script beside it from
+    # oracle/ only) to 1e-11 with the same step count; the gap to Eq.
+    # (Jaffe_noangle) is recorded at each dx and converges to ~0.058 (the
+    # Gaussian-shape ansatz failing at y1 = 0.02), while f itself converges.
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "single_track_dx_sweep.json")))
+    fs = []
+    for r in g["runs"]:
+        nx, nz, dx = r["nx"], r["nz"], r["dx_cm"]
+        with B.Simulation(nx, nx, nz, dx, g["voltage_V"], dt_s=r["dt_s"], precision=B.IT_FP64,
+                          lateral_bc=B.IT_ABSORBING) as sim:
+            c = 0.5 * nx * dx
+            sim.deposit([c], [c], [g["LET_keV_um"]], [g["b_cm"]])
+            steps = sim.run_to_completion(tol=1e-9, check_every=32)
+            t = sim.tallies()
+            print(f"b/dx = {r['b_over_dx']}: steps {steps} f {t.f:.12f} oracle {r['f']:.12f} "
+                  f"f - f_J {t.f - g['f_jaffe']:.5f}")
+            assert steps == r["steps"]
+            assert t.f == pytest.approx(r["f"], abs=1e-11)
+            fs.append(t.f)
+    assert 0.0 < fs[2] - fs[1] < 0.7 * (fs[1] - fs[0])
+    assert 0.05 < fs[2] - g["f_jaffe"] < 0.06
