@@ -267,6 +267,258 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
     }
 }
 
+// TMA-staged float4 z-march over the entries of simulations with nx % 4 == 0
+// and nx <= 256: the batched counterpart of the single-context step kernel.
+// A CTA owns rows [y0, y0 + rows) of one simulation (full width) and planes
+// [z0, z1).  Every plane it needs (z0 - 1 .. z1) arrives by TMA in a ring of
+// shared-memory slots: a box of bt = min(256 / (nx/4), ny) rows per species
+// plus one halo row above and below, wrapped when the faces are periodic;
+// rows and planes outside the simulation's tensor arrive as zeros (the
+// absorbing faces and the electrode ghost planes).  Each simulation's
+// tensor maps (two sets x two species x main/halo box) sit in global memory.
+// The last warp to release a slot refills it with the plane S further on.
+// Thread t owns the float4 x-segment t mod (nx/4) of row t div (nx/4), keeps
+// planes k-1 and k of it in registers and reads x/y neighbours and plane k+1
+// from shared memory: the same per-cell operation sequence as every other
+// kernel.  Every ring wait is bounded (2^32 SM cycles); a wait that runs out
+// raises the error flag, and the CTA drains the copies it issued and returns.
+constexpr int BT_MAX_S = 8;
+constexpr int BT_WARPS = 8;
+// dynamic shared memory of the TMA batched kernel: three CTAs per SM; the
+// ring gets whatever slots fit (3..8; a slot is at most 12 KiB at nx = 256)
+constexpr int kBtSmem = 70 * 1024;
+constexpr int kBtSmemFloats = (kBtSmem - 128) / 4;
+
+__device__ __forceinline__ int bt_align32(int f) { return (f + 31) & ~31; }
+
+template <bool PERIODIC, bool SC>
+__global__ void __launch_bounds__(BT_WARPS * 32, 3)
+step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__restrict__ tab,
+                        const CUtensorMap *__restrict__ maps, int parity, float *__restrict__ op_all,
+                        float *__restrict__ om_all, double *__restrict__ slots, int smem_floats,
+                        int *__restrict__ err) {
+    constexpr int NW = BT_WARPS, WQ = SC ? 16 : 8, NQ = SC ? 9 : 7;
+    extern __shared__ __align__(128) unsigned char bt_smem_raw[];
+    unsigned char *smem_base = bt_smem_raw + ((128u - (smem_u32(bt_smem_raw) & 127u)) & 127u);
+    float *ring = reinterpret_cast<float *>(smem_base);
+    __shared__ double wacc[NW * WQ];
+    __shared__ __align__(8) uint64_t full[BT_MAX_S];
+    __shared__ uint32_t rel[BT_MAX_S], fills[BT_MAX_S];
+    __shared__ volatile int abort_flag;
+    __shared__ BatchSim Sm;
+    __shared__ VecEntry E;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        E = tab[blockIdx.x];
+        Sm = sims[E.sim];
+    }
+    __syncthreads();
+    const int nx = Sm.nx, ny = Sm.ny, nz = Sm.nz;
+    const Coef<float> &c = Sm.cf;
+    const int ncol4 = nx >> 2;
+    const int bt = min(256 / ncol4, ny);           // rows of the main box
+    const int rows = E.rows;                        // rows computed (<= bt)
+    const int reg_main = bt_align32(nx), reg_bot = reg_main + bt_align32(bt * nx), blk = reg_bot + bt_align32(nx);
+    const int slotf = 2 * blk;
+    const int S = min(smem_floats / slotf, BT_MAX_S);   // the host keeps this >= 3
+    const CUtensorMap *mp = maps + (size_t)E.sim * 8 + parity * 4;   // [species][main, halo]
+    const int z0 = E.z0, z1 = E.z1, y0 = E.y0;
+    const int nload = z1 - z0 + 2;                  // planes z0 - 1 .. z1
+    const int ytop = PERIODIC ? (y0 > 0 ? y0 - 1 : ny - 1) : y0 - 1;
+    const int ybot = PERIODIC ? (y0 + rows < ny ? y0 + rows : 0) : y0 + rows;
+    const uint32_t tx = 2u * (uint32_t)(bt + 2) * (uint32_t)nx * 4u;
+
+    // load plane z0 - 1 + n into its slot (one thread)
+    auto issue = [&](int n) {
+        const int p = z0 - 1 + n;
+        const int slot = n % S;
+        float *base = ring + (size_t)slot * slotf;
+        uint64_t *bar = &full[slot];
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, tx);
+        for (int s = 0; s < 2; ++s) {
+            float *b = base + s * blk;
+            tma_load3(b + reg_main, &mp[2 * s], bar, 0, y0, p);
+            tma_load3(b, &mp[2 * s + 1], bar, 0, ytop, p);
+            tma_load3(b + reg_bot, &mp[2 * s + 1], bar, 0, ybot, p);
+        }
+        fills[slot] += 1;
+    };
+
+    if (tid == 0) {
+        for (int q = 0; q < 4; ++q) fence_tensormap_acquire(&mp[q]);
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&full[q], 1);
+            rel[q] = 0;
+            fills[q] = 0;
+        }
+        for (int q = 0; q < NW * WQ; ++q) wacc[q] = 0.0;
+        abort_flag = 0;
+        fence_mbar_init();
+        for (int n = 0; n < S && n < nload; ++n) issue(n);
+    }
+    __syncthreads();
+
+    auto flush = [&](int q, float part) {
+        double v = (double)part;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) wacc[warp * WQ + q] += v;
+    };
+
+    // this thread's float4 segment; threads past the tile repeat its last
+    // row's segment and store nothing
+    const bool valid = tid < rows * ncol4;
+    const int te = valid ? tid : rows * ncol4 - 1;
+    const int ty = te / ncol4, c4 = te - ty * ncol4;
+    const int x0 = 4 * c4;
+    const int o_c = reg_main + ty * nx + x0;
+    const int o_u = ty == 0 ? x0 : reg_main + (ty - 1) * nx + x0;
+    const int o_d = ty == rows - 1 ? reg_bot + x0 : reg_main + (ty + 1) * nx + x0;
+    const int o_l = reg_main + ty * nx + (c4 == 0 ? nx - 1 : x0 - 1);
+    const int o_r = reg_main + ty * nx + (c4 == ncol4 - 1 ? 0 : x0 + 4);
+    const int yg = y0 + ty;
+    const bool edge_u = !PERIODIC && yg == 0, edge_d = !PERIODIC && yg == ny - 1;
+    float *out_[2] = {op_all + Sm.off, om_all + Sm.off};
+    const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
+    uint32_t off = ((uint32_t)z0 * (uint32_t)ny + (uint32_t)yg) * (uint32_t)nx + (uint32_t)x0;
+
+    RingPos pos{0, 0u};
+    int nrel = 0;
+    bool failed = false;
+    auto wait_full = [&](const RingPos &u) {
+        if (failed) return;
+        bool ok = mbar_try_wait(&full[u.slot], u.phase);
+        if (__all_sync(0xffffffffu, ok)) return;
+        const long long t0 = clock64();
+        for (;;) {
+            ok = ok || mbar_try_wait(&full[u.slot], u.phase);
+            if (__all_sync(0xffffffffu, ok)) return;
+            if (__any_sync(0xffffffffu, abort_flag || clock64() - t0 > (1LL << 32))) break;
+        }
+        failed = true;
+        if (lane == 0) abort_flag = 1;
+    };
+    auto release = [&](const RingPos &u) {
+        __syncwarp();
+        if (lane == 0 && !failed) {
+            const uint32_t old = atom_add_acq_rel(&rel[u.slot], 1u);
+            if (old % NW == NW - 1 && nrel + S < nload && !abort_flag) issue(nrel + S);
+        }
+        ++nrel;
+    };
+
+    float4 prev[2], cur[2];
+    wait_full(pos);
+    {
+        const float *sl = ring + (size_t)pos.slot * slotf;
+        prev[0] = *reinterpret_cast<const float4 *>(sl + o_c);
+        prev[1] = *reinterpret_cast<const float4 *>(sl + blk + o_c);
+    }
+    release(pos);
+    pos.advance(S);
+    wait_full(pos);
+    RingPos pc = pos;
+    pos.advance(S);
+    {
+        const float *sl = ring + (size_t)pc.slot * slotf;
+        cur[0] = *reinterpret_cast<const float4 *>(sl + o_c);
+        cur[1] = *reinterpret_cast<const float4 *>(sl + blk + o_c);
+    }
+    float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f, ssum0 = 0.f, ssum1 = 0.f;
+    int nacc = 0;
+    for (int k = z0; k < z1; ++k) {
+        wait_full(pos);
+        const float *sk = ring + (size_t)pc.slot * slotf;
+        const float *sn = ring + (size_t)pos.slot * slotf;
+        float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
+        const float4 P = cur[0], M = cur[1];
+        const float2 rxy = __fmul2_rn(make_float2(P.x, P.y), make_float2(M.x, M.y));
+        const float2 rzw = __fmul2_rn(make_float2(P.z, P.w), make_float2(M.z, M.w));
+        float2 dxy, dzw;
+        if (SC) sc_diff4(P, M, dxy, dzw);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float *bk = sk + s * blk;
+            const float4 n = cur[s];
+            const float4 u = *reinterpret_cast<const float4 *>(bk + o_u);
+            const float4 d = *reinterpret_cast<const float4 *>(bk + o_d);
+            const float4 zp = *reinterpret_cast<const float4 *>(sn + s * blk + o_c);
+            float l = bk[o_l];
+            float r = bk[o_r];
+            if (!PERIODIC) {
+                if (c4 == 0) l = 0.f;
+                if (c4 == ncol4 - 1) r = 0.f;
+            }
+            float4 v = upd7x4(n, l, r, u, d, prev[s], zp, rxy, rzw, c.wc[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s],
+                              c.adt);
+            if (SC) {
+                float2 pxy, pzw;
+                v = add_sc4(v, c.sc[s], n, dxy, dzw, pxy, pzw);
+                if (valid) (s ? ssum1 : ssum0) += (pxy.x + pxy.y) + (pzw.x + pzw.y);
+            }
+            if (valid) {
+                *reinterpret_cast<float4 *>(out_[s] + off) = v;
+                if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
+                if (!PERIODIC) {
+                    if (c4 == 0) lat[s] += n.x;
+                    if (c4 == ncol4 - 1) lat[s] += n.w;
+                    if (edge_u) lat[s] += (n.x + n.y) + (n.z + n.w);
+                    if (edge_d) lat[s] += (n.x + n.y) + (n.z + n.w);
+                }
+            }
+            prev[s] = n;
+            cur[s] = zp;
+        }
+        if (valid) rsum += (rxy.x + rxy.y) + (rzw.x + rzw.y);
+        off += plane;
+        if (!PERIODIC) { lsum0 += lat[0]; lsum1 += lat[1]; }
+        if (++nacc == 32) {
+            flush(0, rsum);
+            rsum = 0.f;
+            if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); lsum0 = lsum1 = 0.f; }
+            if (SC) { flush(7, ssum0); flush(8, ssum1); ssum0 = ssum1 = 0.f; }
+            nacc = 0;
+        }
+        if (k == 0) { flush(1, an[0]); flush(2, an[1]); }
+        if (k == nz - 1) { flush(3, an[0]); flush(4, an[1]); }
+        release(pc);
+        pc = pos;
+        pos.advance(S);
+    }
+    flush(0, rsum);
+    if (!PERIODIC) { flush(5, lsum0); flush(6, lsum1); }
+    if (SC) { flush(7, ssum0); flush(8, ssum1); }
+    release(pc);   // plane z1
+    if (failed && lane == 0) atomicExch(err, 1);
+    __syncthreads();
+    if (tid == 0) {
+        // no copy may be in flight when the CTA exits
+        for (int j = 0; j < S; ++j)
+            if (fills[j] > 0) (void)mbar_wait_bounded(&full[j], (fills[j] - 1u) & 1u);
+    }
+    if (tid == 0 && !abort_flag) {
+        double acc[NQ];
+        for (int q = 0; q < NQ; ++q) {
+            double v = 0.0;
+            for (int w = 0; w < NW; ++w) v += wacc[w * WQ + q];
+            acc[q] = v;
+        }
+        double *sl = slots + (size_t)blockIdx.x * NT;
+        sl[0] += acc[0] * c.rec_f;
+        sl[1] += acc[1] * c.anode_f[0];
+        sl[2] += acc[2] * c.anode_f[1];
+        sl[3] += acc[3] * c.cathode_f[0];
+        sl[4] += acc[4] * c.cathode_f[1];
+        sl[5] += acc[5] * c.latx_f[0];
+        sl[6] += acc[6] * c.latx_f[1];
+        if (SC) {
+            sl[7] += acc[NQ - 2] * c.sc_f[0];
+            sl[8] += acc[NQ - 1] * c.sc_f[1];
+        }
+    }
+}
+
 // Fold the slots of each active simulation's entries (contiguous in the
 // table, in order) into its FP64 accumulators and clear them.  One block
 // per active simulation, one thread per tally.
@@ -352,6 +604,7 @@ struct it_batch {
     // work tables of the current segment
     std::vector<BatchEntry> tab;      // row ranges of every active simulation (monitors)
     std::vector<int> mfirst, mcount;  // per active simulation, into tab
+    std::vector<int> morder;          // the active simulation of each mfirst/mcount entry
     std::vector<VecEntry> vtab;       // step entries of the float4 kernel
     std::vector<BatchEntry> stab;     // step entries of the scalar kernel
     std::vector<int> first, count, sim_of;   // per active simulation, into the step slots
@@ -381,6 +634,15 @@ struct it_batch {
     double *d_plane, *d_tracks, *d_wx, *d_wy;
     int64_t track_cap;
     int max_nx, max_ny;
+    // TMA-staged float4 kernel: per simulation [set][species][main, halo]
+    // tensor maps (zero for simulations it does not take), its use, the
+    // number of leading float4 entries it runs, and the device error flag of
+    // its bounded waits
+    CUtensorMap *d_maps;
+    std::vector<char> tma_ok;
+    int use_tma;
+    int nvt;
+    int *d_err;
 };
 
 namespace {
@@ -395,7 +657,7 @@ int bfail(int code, const std::string &m) {
 // rows, split in z when few cells are active), the scalar kernel the rest.
 // All entries of one simulation are contiguous, so the fold is in order.
 int build_table(it_batch *b) {
-    b->tab.clear(); b->mfirst.clear(); b->mcount.clear();
+    b->tab.clear(); b->mfirst.clear(); b->mcount.clear(); b->morder.clear();
     b->vtab.clear(); b->stab.clear();
     b->first.clear(); b->count.clear(); b->sim_of.clear();
     long long active_cells = 0, vec_tiles = 0;
@@ -416,8 +678,13 @@ int build_table(it_batch *b) {
     const long long zsplit =
         vec_tiles > 0 ? std::max(1LL, ((long long)b->vec_cps * sms + vec_tiles - 1) / vec_tiles) : 1;
     std::vector<int> vfirst, vcount, sfirst, scount, vsim, ssim;
-    for (int s = 0; s < b->nsim; ++s) {
-        if (!b->active[s]) continue;
+    // float4 entries of the simulations the TMA kernel takes come first
+    b->nvt = 0;
+    std::vector<int> order;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int s = 0; s < b->nsim; ++s)
+            if (b->active[s] && ((b->use_tma && b->tma_ok[s]) == (pass == 0))) order.push_back(s);
+    for (int s : order) {
         const BatchSim &h = b->hs[s];
         const long long rows = (long long)h.ny * h.nz;
         const long long rpe = std::max(1LL, chunk / h.nx);
@@ -425,6 +692,7 @@ int build_table(it_batch *b) {
         int n = 0;
         for (long long r0 = 0; r0 < rows; r0 += rpe, ++n) b->tab.push_back(BatchEntry{s, 0, r0, std::min(rows, r0 + rpe)});
         b->mcount.push_back(n);
+        b->morder.push_back(s);
         if (h.nx % 4 == 0 && h.nx <= 1024) {
             const int rpt = std::max(1, 256 / (h.nx / 4));
             const int zc = (int)std::min<long long>(zsplit, std::max(1, h.nz / 8));
@@ -436,6 +704,7 @@ int build_table(it_batch *b) {
                     b->vtab.push_back(VecEntry{s, y0, std::min(rpt, h.ny - y0), (int)((long long)h.nz * q / zc),
                                                (int)((long long)h.nz * (q + 1) / zc), 0});
             vcount.push_back(m);
+            if (b->use_tma && b->tma_ok[s]) b->nvt += m;
         } else {
             ssim.push_back(s);
             sfirst.push_back((int)b->stab.size());
@@ -492,15 +761,22 @@ int build_table(it_batch *b) {
 }
 
 int launch_batched_step(it_batch *b, int parity) {
-    const int nv = (int)b->vtab.size(), ns = (int)b->stab.size();
+    const int nv = (int)b->vtab.size(), ns = (int)b->stab.size(), nt = b->nvt;
     const float *ip = b->state[parity][0], *im = b->state[parity][1];
     float *op = b->state[parity ^ 1][0], *om = b->state[parity ^ 1][1];
     const bool per = b->p.lateral_bc == IT_PERIODIC;
     const bool sc = b->p.space_charge != 0;
-    if (nv) {
+    if (nt) {
+        auto *kt = per ? (sc ? step_batched_tma_kernel<true, true> : step_batched_tma_kernel<true, false>)
+                       : (sc ? step_batched_tma_kernel<false, true> : step_batched_tma_kernel<false, false>);
+        kt<<<nt, BT_WARPS * 32, kBtSmem, b->stream>>>(b->d_sims, b->d_vtab, b->d_maps, parity, op, om, b->d_slots,
+                                                     kBtSmemFloats, b->d_err);
+        IT_CK(cudaGetLastError());
+    }
+    if (nv > nt) {
         auto *kv = per ? (sc ? step_batched_vec_kernel<true, true> : step_batched_vec_kernel<true, false>)
                        : (sc ? step_batched_vec_kernel<false, true> : step_batched_vec_kernel<false, false>);
-        kv<<<nv, 256, 0, b->stream>>>(b->d_sims, b->d_vtab, ip, im, op, om, b->d_slots);
+        kv<<<nv - nt, 256, 0, b->stream>>>(b->d_sims, b->d_vtab + nt, ip, im, op, om, b->d_slots + (size_t)NT * nt);
         IT_CK(cudaGetLastError());
     }
     if (ns) {
@@ -562,13 +838,16 @@ static int ladder_batch(it_batch *b) {
     std::vector<float> mx(ne);
     IT_CK(cudaMemcpyAsync(mx.data(), b->d_max, sizeof(float) * ne, cudaMemcpyDeviceToHost, b->stream));
     IT_CK(cudaStreamSynchronize(b->stream));
-    int a = 0;
-    for (int s = 0; s < b->nsim; ++s) {
-        if (!b->active[s]) continue;
+    for (size_t a = 0; a < b->morder.size(); ++a) {
+        const int s = b->morder[a];
         double nmax = -INFINITY;
         for (int q = b->mfirst[a]; q < b->mfirst[a] + b->mcount[a]; ++q) nmax = std::max(nmax, (double)mx[q]);
-        ++a;
-        const bool pending = b->pulse_done[s] >= 1 && b->pulse_done[s] < b->pulse_count[s];
+        // as in a single context, whose check runs before the deposits of its
+        // step: a check at the step of the last pulse still counts that pulse
+        // as to come
+        const bool last_now = b->pulse_count[s] > 1 && b->pulse_done[s] == b->pulse_count[s] &&
+                              b->steps[s] == (int64_t)(b->pulse_count[s] - 1) * b->pulse_period[s];
+        const bool pending = (b->pulse_done[s] >= 1 && b->pulse_done[s] < b->pulse_count[s]) || last_now;
         if (pending) continue;
         const it_sim_desc &d = b->desc[s];
         it_params p = b->p;
@@ -603,15 +882,16 @@ int in_domain(it_batch *b, std::vector<double> &ind2) {
                                                     b->d_mon);
     IT_CK(cudaGetLastError());
     std::vector<double> mon(2 * (size_t)ne);
+    int err = 0;
     IT_CK(cudaMemcpyAsync(mon.data(), b->d_mon, sizeof(double) * 2 * ne, cudaMemcpyDeviceToHost, b->stream));
+    IT_CK(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     IT_CK(cudaStreamSynchronize(b->stream));
-    int a = 0;
-    for (int s = 0; s < b->nsim; ++s) {
-        if (!b->active[s]) continue;
+    if (err) return bfail(IT_ETIMEOUT, "a bounded device wait ran out in the batched step kernel");
+    for (size_t a = 0; a < b->morder.size(); ++a) {
+        const int s = b->morder[a];
         const double vol = b->dx[s] * b->dx[s] * b->dx[s];
         double p = 0, m = 0;
         for (int e = b->mfirst[a]; e < b->mfirst[a] + b->mcount[a]; ++e) { p += mon[2 * e]; m += mon[2 * e + 1]; }
-        ++a;
         ind2[2 * s] = p * vol;
         ind2[2 * s + 1] = m * vol;
     }
@@ -628,6 +908,7 @@ void batch_free(it_batch *b) {
     cudaFree(b->d_vtab); cudaFree(b->d_stab);
     cudaFree(b->d_first); cudaFree(b->d_count); cudaFree(b->d_simof);
     cudaFree(b->d_plane); cudaFree(b->d_tracks); cudaFree(b->d_wx); cudaFree(b->d_wy);
+    cudaFree(b->d_maps); cudaFree(b->d_err);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -717,6 +998,41 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
         (e = cudaMemsetAsync(b->d_rel, 0, sizeof(double) * 8 * nsim, b->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
         return bail(e, "batch setup");
+    // tensor maps of the TMA batched kernel: simulations with nx % 4 == 0 and
+    // nx <= 256 (one box spans the row); boxes of min(256 / (nx/4), ny) rows
+    // and of one halo row
+    b->tma_ok.assign(nsim, 0);
+    b->use_tma = 1;
+    {
+        std::vector<CUtensorMap> maps((size_t)nsim * 8);
+        std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+        for (int s = 0; s < nsim; ++s) {
+            const BatchSim &h = b->hs[s];
+            if (h.nx % 4 != 0 || h.nx > 256) continue;
+            const int rows = std::min(256 / (h.nx / 4), h.ny);
+            int rc = IT_OK;
+            for (int set = 0; set < 2 && rc == IT_OK; ++set)
+                for (int sp = 0; sp < 2 && rc == IT_OK; ++sp) {
+                    float *base_s = b->state[set][sp] + h.off;
+                    rc = encode_map(&maps[(size_t)s * 8 + set * 4 + sp * 2], base_s, h.nx, h.ny, h.nz, h.nx, rows);
+                    if (rc == IT_OK)
+                        rc = encode_map(&maps[(size_t)s * 8 + set * 4 + sp * 2 + 1], base_s, h.nx, h.ny, h.nz, h.nx, 1);
+                }
+            if (rc) { batch_free(b); return rc; }
+            b->tma_ok[s] = 1;
+        }
+        if ((e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * maps.size())) != cudaSuccess ||
+            (e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess ||
+            (e = cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                                 b->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+            return bail(e, "batch tensor maps");
+        for (auto *k : {step_batched_tma_kernel<true, true>, step_batched_tma_kernel<true, false>,
+                        step_batched_tma_kernel<false, true>, step_batched_tma_kernel<false, false>})
+            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kBtSmem)) != cudaSuccess)
+                return bail(e, "cudaFuncSetAttribute(batched TMA kernel)");
+    }
     b->tab_dirty = true;
     *out = b;
     return IT_OK;
@@ -874,13 +1190,15 @@ int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us) {
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         rc = cuda_fail(cudaGetLastError(), "batch autotune set-up");
     const long long chunk0 = b->chunk;
-    const int cps0 = b->vec_cps;
+    const int cps0 = b->vec_cps, tma0 = b->use_tma;
     long long best_chunk = chunk0;
-    int best_cps = cps0;
+    int best_cps = cps0, best_tma = tma0;
     double best = 1e300;
+    for (int tma : {1, 0})
     for (int cps : {1, 2, 4, 8, 16, 32}) {
         for (long long chunk : {4096LL, 16384LL, 65536LL}) {
             if (rc) break;
+            b->use_tma = tma;
             b->vec_cps = cps;
             b->chunk = chunk;
             rc = build_table(b);
@@ -902,6 +1220,7 @@ int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us) {
                 best = ms * 1e3 / K;
                 best_chunk = chunk;
                 best_cps = cps;
+                best_tma = tma;
             }
         }
     }
@@ -912,6 +1231,7 @@ int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us) {
     // the chosen shape; the next table build also clears the trial tallies
     b->chunk = rc ? chunk0 : best_chunk;
     b->vec_cps = rc ? cps0 : best_cps;
+    b->use_tma = rc ? tma0 : best_tma;
     b->tab_dirty = true;
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     if (rc) return rc;

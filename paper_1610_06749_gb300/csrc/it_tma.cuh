@@ -59,6 +59,11 @@ __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, uin
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// a tensor map read from global memory: order its bytes (written before the
+// launch) before the tensor-map proxy reads them
+__device__ __forceinline__ void fence_tensormap_acquire(const void *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 

@@ -122,3 +122,33 @@ def test_ladder_batch_equals_single_contexts_bitwise(bc):
                 for s in range(2):
                     assert np.array_equal(bt.density(q, s), g.density(s)), f"sim {q} species {s}"
                 assert tb.f == pytest.approx(ts.f, abs=1e-7)
+
+
+def test_ladder_batch_pulse_train_equals_single_context_bitwise():
+    # a train of 4 pulses: the ladder applies only once the last pulse is in;
+    # the batch's check at the step of the last pulse, which runs after that
+    # pulse's deposit, counts it as still to come exactly like a context,
+    # whose check runs before the deposits of its step
+    nx, ny, nz, dx, V, P = 32, 32, 30, 5e-4, 150.0, 128
+    tr = synth.uniform_tracks(931, 9, nx * dx, ny * dx, 1e-3, let="loguniform")
+    tr.let_keV_um[:] = np.maximum(tr.let_keV_um, 50.0)
+    d = dict(nx=nx, ny=ny, nz=nz, dx_cm=dx, voltage_V=V)
+    with B.Batch([d], scheme=B.IT_UPWIND, dt_ladder=True, react_kappa=0.0625) as bt:
+        bt.deposit(0, tr.x_cm, tr.y_cm, tr.let_keV_um, tr.b_cm)
+        bt.set_pulses(0, 4, P)
+        bt.retime()
+        dt0 = bt.tallies(0).dt_s
+        bt.run(tol=1e-6, check_every=64)
+        tb = bt.tallies(0)
+        with B.Simulation(nx, ny, nz, dx, V, dt_s=dt0, scheme=B.IT_UPWIND, dt_ladder=True, react_kappa=0.0625) as g:
+            n = len(tr)
+            g.schedule(np.tile(tr.x_cm, 4), np.tile(tr.y_cm, 4), np.tile(tr.let_keV_um, 4), np.tile(tr.b_cm, 4),
+                       np.repeat(np.arange(4, dtype=np.int64) * P, n))
+            g.run_to_completion(tol=1e-6, check_every=64)
+            ts = g.tallies()
+            log = g.dt_log()
+            assert len(log) >= 2 and log[1][0] > 3 * P, log
+            assert ts.steps == tb.steps and ts.dt_s == tb.dt_s
+            for s in range(2):
+                assert np.array_equal(bt.density(0, s), g.density(s))
+            assert tb.f == pytest.approx(ts.f, abs=1e-7)
