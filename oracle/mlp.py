@@ -9,9 +9,13 @@ weights.  Parameters per member, in order:
     W4 [256][256], b4, W5 [1][256], b5 [1]
 (W stored out-features x in-features).
 
-``quant=True`` applies the precision points of the GPU path -- weights and
-every layer input rounded to bfloat16, the backward error signals rounded to
-bfloat16 before they enter a matrix product -- while every sum is FP64.
+``quant=True`` applies the precision points of the GPU path, while every sum
+is FP64: weights rounded to bfloat16; every layer input (the normalised
+inputs and each SiLU output, first rounded to float32) carried as the
+two-term bfloat16 expansion hi + lo, hi = bf16(a), lo = bf16(a - hi), in the
+forward pass and in the output layer's weight gradient; the one-term hi
+part in the weight gradients of the hidden layers; the backward error
+signals rounded to bfloat16 before they enter a matrix product.
 ``quant=False`` is plain FP64 (pinned against finite differences).
 """
 from __future__ import annotations
@@ -42,6 +46,16 @@ def bf16(x) -> np.ndarray:
     return out
 
 
+def bf16_split(x) -> np.ndarray:
+    """The two-term bfloat16 expansion hi + lo of float32(x): hi = bf16(x),
+    lo = bf16(x - hi) (the difference is exact in float32).  Represents
+    float32(x) to within 2^-16 of |x| (one bf16 rounding of a residual at most
+    2^-9 of |x|)."""
+    f = np.asarray(x, dtype=np.float32).astype(np.float64)
+    hi = bf16(f)
+    return hi + bf16(f - hi)
+
+
 def unpack(theta: np.ndarray):
     out, o = [], 0
     for s in SHAPES:
@@ -65,19 +79,26 @@ def dsilu(z):
 
 
 def forward(theta, X, quant=False):
-    """X: [B][6] normalised inputs.  Returns (fhat [B], cache)."""
-    q = bf16 if quant else (lambda a: np.asarray(a, dtype=np.float64))
+    """X: [B][6] normalised inputs.  Returns (fhat [B], cache): the cache
+    holds the pre-activations, the layer inputs as the forward pass used them
+    (hi + lo when quantised) and their one-term bf16 (hi) parts."""
+    ident = lambda a: np.asarray(a, dtype=np.float64)
+    q = bf16 if quant else ident
+    qa = bf16_split if quant else ident
     W1, b1, W2, b2, W3, b3, W4, b4, W5, b5 = unpack(np.asarray(theta, dtype=np.float64))
-    A = q(X)
-    Zs, As = [], [A]
+    a = np.asarray(X, dtype=np.float64)
+    A = qa(a)
+    Zs, As, His = [], [A], [q(a)]
     for W, b in ((W1, b1), (W2, b2), (W3, b3), (W4, b4)):
         Z = A @ q(W).T + b
-        A = q(silu(Z))
+        s = silu(Z)
+        A = qa(s)
         Zs.append(Z)
         As.append(A)
+        His.append(q(s))
     z = A @ q(W5).T[:, 0] + b5[0]
     fhat = 1.0 / (1.0 + np.exp(-z))
-    return fhat, (Zs, As, z)
+    return fhat, (Zs, As, His, z)
 
 
 def loss_and_grad(theta, X, y, quant=False):
@@ -85,7 +106,7 @@ def loss_and_grad(theta, X, y, quant=False):
     q = bf16 if quant else (lambda a: np.asarray(a, dtype=np.float64))
     theta = np.asarray(theta, dtype=np.float64)
     W1, b1, W2, b2, W3, b3, W4, b4, W5, b5 = unpack(theta)
-    fhat, (Zs, As, z) = forward(theta, X, quant)
+    fhat, (Zs, As, His, z) = forward(theta, X, quant)
     B = X.shape[0]
     loss = float(np.mean((fhat - y) ** 2))
     dz = 2.0 / B * (fhat - y) * fhat * (1.0 - fhat)          # through the output sigmoid
@@ -97,7 +118,7 @@ def loss_and_grad(theta, X, y, quant=False):
     for l in (3, 2, 1, 0):
         dZ = dA * dsilu(Zs[l])
         dZq = q(dZ)
-        grads[2 * l] = dZq.T @ As[l]                             # dW [out][in]
+        grads[2 * l] = dZq.T @ His[l]                            # dW [out][in], hi part of the input
         grads[2 * l + 1] = dZ.sum(axis=0)                        # db from the unrounded signal
         if l > 0:
             dA = dZq @ q(Ws[l])

@@ -55,6 +55,25 @@ def test_bf16_rounding_matches_torch():
     np.testing.assert_array_equal(M.bf16(x), ref)
 
 
+def test_bf16_split_two_term_expansion():
+    # hi + lo with hi = bf16(x), lo = bf16(x - hi): torch computes the same two
+    # roundings independently; the pair carries float32(x) to within 2^-16 of
+    # |x| and exactly when x needs at most 16 significant bits
+    torch = pytest.importorskip("torch")
+    u = synth.uniform01(9, 3000)
+    x = (u - 0.5) * 10.0 ** np.linspace(-5, 5, 3000)
+    f = torch.tensor(x, dtype=torch.float32)
+    hi = f.to(torch.bfloat16)
+    lo = (f - hi.to(torch.float32)).to(torch.bfloat16)
+    ref = hi.to(torch.float64).numpy() + lo.to(torch.float64).numpy()
+    got = M.bf16_split(x)
+    np.testing.assert_array_equal(got, ref)
+    x32 = x.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(got - x32) <= 2.0 ** -16 * np.abs(x32))
+    exact = np.array([1.0 + 2 ** -15, -3.0 * (1 + 2 ** -13), 0.0, 2 ** -20 * (1 + 2 ** -10)])
+    np.testing.assert_array_equal(M.bf16_split(exact), exact)
+
+
 def test_adam_first_step_moves_by_lr_times_sign():
     # after the first step m_hat / sqrt(v_hat) = g/|g|: the update is lr*sign(g)
     a = M.Adam(3, lr=0.01)
@@ -69,7 +88,7 @@ def test_quantised_forward_is_close_to_fp64_and_learns_nothing_wrong():
     f0, _ = M.forward(theta, X, quant=False)
     f1, _ = M.forward(theta, X, quant=True)
     assert np.all((f0 > 0) & (f0 < 1))
-    assert np.max(np.abs(f0 - f1)) < 2e-2          # bfloat16 inputs and weights
+    assert np.max(np.abs(f0 - f1)) < 2e-2          # bfloat16 weights, two-term bfloat16 activations
     # a few Adam steps on the quantised gradient lower the loss
     opt = M.Adam(theta.size, lr=1e-3)
     l0 = M.loss_and_grad(theta, X, y, quant=True)[0]
