@@ -174,6 +174,8 @@ int zmarch_configure(it_ctx *c);
 int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid);
 // FP32 3-D tensor map over [nz][ny][nx] with a box of bx x rows x 1 (it_zmarch.cu)
 int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx, int rows);
+int encode_bf16_sw128(CUtensorMap *m, const void *base, long long K, long long rows, long long members,
+                      long long row_bytes, long long member_bytes);
 // two steps per launch (it_zmarch2.cu)
 int zmarch2_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid);
 int launch_step_zmarch2(it_ctx *c, cudaStream_t s);

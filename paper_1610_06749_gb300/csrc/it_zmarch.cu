@@ -382,6 +382,30 @@ int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx, int r
     return IT_OK;
 }
 
+// bf16 operand of the tensor-core GEMM (it_tc.cuh): dims {K, rows, members}
+// (K contiguous), byte strides of a row and of a member, boxes of 64 x 128
+// with the 128-byte swizzle; rows and K beyond the dims arrive as zeros.
+int encode_bf16_sw128(CUtensorMap *m, const void *base, long long K, long long rows, long long members,
+                      long long row_bytes, long long member_bytes) {
+    auto fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available");
+        return IT_ECUDA;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)members};
+    cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)member_bytes};
+    cuuint32_t box[3] = {64, 128, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled (bf16 operand) failed (code " + std::to_string((int)r) + ")");
+        return IT_ECUDA;
+    }
+    return IT_OK;
+}
+
 static int align32f(int floats) { return (floats + 31) / 32 * 32; }   // 128-byte multiple of floats
 
 // The dynamic shared-memory limit is a property of the kernel function,
