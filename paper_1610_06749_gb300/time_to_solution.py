@@ -18,6 +18,7 @@ stopped being finite is reported as unstable.  Every step runs in the CUDA
 solver; this module only sets the runs up and reports.
 
     python -m paper_1610_06749_gb300.time_to_solution [V ...]
+    python -m paper_1610_06749_gb300.time_to_solution sweep
 """
 from __future__ import annotations
 
@@ -54,8 +55,25 @@ def run(V: float, scheme: int, kappa: float, ladder: bool, max_steps: int = 2_00
     return out
 
 
+def sweep(volts=(50.0, 100.0, 200.0, 300.0, 400.0)):
+    """The pulsed workload's voltage sweep run to completion: upwind with the
+    fixed recombination-bound step (kappa = 0.5), upwind with the ladder at
+    kappa = 1/16, and the paper's Lax-Wendroff drift with the ladder at
+    kappa = 1/8."""
+    out = []
+    for V in volts:
+        for scheme, kappa, ladder in ((B.IT_UPWIND, 0.5, False), (B.IT_UPWIND, 0.0625, True),
+                                      (B.IT_LAX_WENDROFF, 0.125, True)):
+            r = run(V, scheme, kappa, ladder, max_steps=400_000)
+            print(json.dumps(r), flush=True)
+            out.append(r)
+    return out
+
+
 def main(argv=None):
     argv = sys.argv[1:] if argv is None else argv
+    if argv and argv[0] == "sweep":
+        return sweep()
     volts = [float(a) for a in argv] or [50.0, 200.0]
     for V in volts:
         # upwind: fixed steps down to kappa = 0.125 give the convergence in dt
