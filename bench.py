@@ -229,6 +229,9 @@ def continuous_roofline(B, synth, dev, steps=500):
         sim.close()
 
 
+LADDER_KAPPA = 0.0625
+
+
 def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=None):
     """Solves/s of the 256-simulation batch (uneven grids 32^3 .. 128x128x200,
     one launch per step for all running simulations, CUDA-graph segments)
@@ -251,8 +254,8 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
         sims.append(dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], dx_cm=d["dx_cm"], voltage_V=d["voltage_V"],
                          n_peak_cm3=B.it_peak_density(tr.let_keV_um, tr.b_cm)))
 
-    def run_batch(idx, ladder=False):
-        bt = B.Batch([sims[q] for q in idx], scheme=scheme, dt_ladder=ladder)
+    def run_batch(idx, ladder=False, kappa=0.5):
+        bt = B.Batch([sims[q] for q in idx], scheme=scheme, dt_ladder=ladder, react_kappa=kappa)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k, q in enumerate(idx):
@@ -269,8 +272,14 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
         return el, out, launches, (ta, tune_us)
 
     t_all, tal_all, launches, tune = run_batch(list(range(len(sims))))
-    # the same 256 simulations with the doubling dt ladder of the runs to completion
-    t_lad, tal_lad, launches_lad, _ = run_batch(list(range(len(sims))), ladder=True)
+    # the same 256 simulations with the doubling dt ladder of the runs to completion at
+    # kappa = 1/16, judged against the fixed step at the same kappa (every step of both keeps
+    # alpha dt n_max <= kappa).  The fixed step at kappa = 0.5 is itself off by up to 1.5e-2 on
+    # the simulations that finish in a few dozen steps, so it is no reference for 1e-3.
+    t_lad, tal_lad, launches_lad, _ = run_batch(list(range(len(sims))), ladder=True, kappa=LADDER_KAPPA)
+    t_fk, tal_fk, launches_fk, _ = run_batch(list(range(len(sims))), ladder=False, kappa=LADDER_KAPPA)
+    df_lad = max(abs(a.f - b.f) for a, b in zip(tal_lad, tal_fk))
+    df_k05 = max(abs(a.f - b.f) for a, b in zip(tal_all, tal_fk))
     sub = list(range(n_subset))
     t_bsub, tal_bsub, _, _ = run_batch(sub)
     ctxs = [B.Simulation(sims[q]["nx"], sims[q]["ny"], sims[q]["nz"], sims[q]["dx_cm"], sims[q]["voltage_V"],
@@ -301,9 +310,17 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
             "subset_plain_solves_per_s": n_subset / t_plain,
             "speedup_vs_plain": (n_subset / t_bsub) / (n_subset / t_plain),
             "max_abs_df_vs_plain": df, "df_bound": 1e-3, "scheme": "upwind" if scheme == B.IT_UPWIND else "lax-wendroff",
-            "ladder": {"solves_per_s": len(sims) / t_lad, "seconds": t_lad, "step_launches": launches_lad,
-                       "speedup_vs_fixed_dt": t_all / t_lad,
-                       "max_abs_df_vs_fixed_dt": max(abs(a.f - b.f) for a, b in zip(tal_lad, tal_all))}}
+            # the ladder's speedup is reported only when its answers stay within df_bound of the
+            # fixed-step batch; otherwise the line says so instead of giving a rate
+            "ladder": {"kappa": LADDER_KAPPA, "step_launches": launches_lad,
+                       "fixed_dt_same_kappa": {"seconds": t_fk, "step_launches": launches_fk,
+                                               "solves_per_s": len(sims) / t_fk},
+                       "max_abs_df_vs_fixed_dt_same_kappa": df_lad, "within_df_bound": df_lad <= 1e-3,
+                       "fixed_kappa_0.5_max_abs_df_vs_kappa_1/16": df_k05,
+                       "solves_per_s": len(sims) / t_lad if df_lad <= 1e-3 else None,
+                       "seconds": t_lad,
+                       "speedup_vs_fixed_dt_same_kappa": t_fk / t_lad if df_lad <= 1e-3 else None,
+                       "speedup_vs_fixed_dt_kappa_0.5": t_all / t_lad if df_lad <= 1e-3 else None}}
 
 
 def time_to_solution(V):
@@ -319,15 +336,19 @@ def time_to_solution(V):
             "abs_df": abs(fixed["f"] - lad["f"]) if fixed["f"] is not None and lad["f"] is not None else None}
 
 
-def surrogate_vs_plain(n_train=2000, n_test=200, epochs=800, plain_sample=40):
+def surrogate_vs_plain(n_train=48000, n_test=2000, epochs=2000, plain_sample=40):
     """The surrogate ensemble (trained on batched-solver runs of the
     surrogate workload) answering held-out configurations, falling back to the
-    plain solver where its members disagree by more than 1e-3, against the
-    plain solver alone.  Reduced sizes; the full 20k/2k run is
-    `python -m paper_1610_06749_gb300.surrogate`."""
+    solver where its members disagree beyond the calibrated gate, against the
+    batched and the plain solver alone.  The single-pulse half of the draws
+    (about 24000 training and 1000 held-out configurations; trains of pulses
+    carry ~25x the solver work); the full 20k/2k study,
+    trains included, is `python -m paper_1610_06749_gb300.surrogate`.  The
+    gains are reported only while the accepted answers meet the 99 %
+    coverage within 1e-3."""
     from paper_1610_06749_gb300 import surrogate as S
     out = S.main(["--train", str(n_train), "--test", str(n_test), "--epochs", str(epochs),
-                  "--plain-sample", str(plain_sample)], quiet=True)
+                  "--plain-sample", str(plain_sample), "--single-pulse", "--val-frac", "0.15"], quiet=True)
     return out
 
 

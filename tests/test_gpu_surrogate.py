@@ -1,39 +1,63 @@
 """The surrogate workflow on solver data: what the trained ensemble gains
 over the solver alone, and that falling back to the solver keeps the answers
-at the solver's value."""
+at the solver's value.
+
+A 5-member ensemble is trained on batched-solver runs of the surrogate
+workload (synth.surrogate_configs: the six inputs of the batched generator,
+runs to completion with the dt ladder) and answers held-out configurations:
+an answer is accepted when the members' spread is within the gate
+calibrated on a held-out slice of the training runs (Clopper-Pearson lower
+bound of the fraction within 1e-3 at 95 % confidence >= 0.99), else the
+configuration falls back to the solver.  The gain is measured against the
+batched solver alone on the same held-out configurations.
+
+The test keeps the single-pulse half of the workload's draws: a train's four
+pulses run at its first time step for up to 1.5 million steps, so the trains
+carry ~25x the solver work of the single pulses, far beyond a test's budget.
+The full workload, trains included, is the 20000/2000 study of
+`python -m paper_1610_06749_gb300.surrogate`.
+"""
 import time
 
 import numpy as np
 import pytest
 
-from paper_1610_06749_gb300 import binding as B
 from paper_1610_06749_gb300 import surrogate as S
 from paper_1610_06749_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+N_DRAW_TRAIN, N_DRAW_TEST, EPOCHS = 48000, 2000, 2000
+
+
+def single_pulses(seed, n):
+    return [c for c in synth.surrogate_configs(seed, n) if c["pulses"] == 1]
 
 
 @pytest.fixture(scope="module")
 def trained():
     from paper_1610_06749_gb300 import build
     build.build()
-    tr = synth.surrogate_configs(1610067493, 1500)
-    te = synth.surrogate_configs(1610067494, 60)
+    tr = single_pulses(1610067493, N_DRAW_TRAIN)
+    te = single_pulses(1610067494, N_DRAW_TEST)
     f_tr, dt_tr, p_tr = S.solve_batch(tr)
+    t0 = time.perf_counter()
     f_te, dt_te, p_te = S.solve_batch(te)
+    t_batch = time.perf_counter() - t0
     sur = S.Surrogate(members=5)
-    loss = sur.fit(S.features(tr, dt_tr, p_tr), f_tr, epochs=600, lr=2e-3, lr_min=1e-5, val_frac=0.1)
-    yield dict(sur=sur, te=te, f_te=f_te, dt_te=dt_te, p_te=p_te, loss=loss)
+    loss = sur.fit(S.features(tr, dt_tr, p_tr), f_tr, epochs=EPOCHS, lr=2e-3, lr_min=1e-5, val_frac=0.15)
+    yield dict(sur=sur, te=te, f_te=f_te, dt_te=dt_te, p_te=p_te, loss=loss, t_batch=t_batch)
     sur.close()
 
 
 def test_training_converges_and_generalises(trained):
     loss = trained["loss"]
-    assert loss[-1] < 0.02 * loss[0]
+    assert loss[-1] < 0.01 * loss[0]
     X = S.features(trained["te"], trained["dt_te"], trained["p_te"])
     mean, spread = trained["sur"].predict(X)
     err = np.abs(mean - trained["f_te"])
-    assert np.median(err) < 1e-2           # held-out configurations, 1500 training runs
+    print(f"held-out error of the ensemble mean: median {np.median(err):.2e}, p90 {np.quantile(err, 0.9):.2e}")
+    assert np.median(err) < 5e-4
     assert np.all(spread >= 0)
 
 
@@ -45,25 +69,37 @@ def test_prediction_is_orders_of_magnitude_faster_than_solving(trained):
     trained["sur"].predict(X)
     t_pred = time.perf_counter() - t0
     t0 = time.perf_counter()
-    for c, d, p in zip(te[:6], dt[:6], per[:6]):
+    for c, d, p in zip(te[:4], dt[:4], per[:4]):
         S.solve_plain(c, d, p)
-    t_solve = (time.perf_counter() - t0) / 6
+    t_solve = (time.perf_counter() - t0) / 4
     assert t_pred / len(te) < 1e-3 * t_solve
+
+
+def test_surrogate_with_fallback_answers_faster_than_the_batched_solver_within_1e3(trained):
+    # the method with the trained network (answers within the gate, the rest
+    # solved in one batch) against the method without it (every
+    # configuration in one batch): a higher answer rate, and at least 99 % of
+    # all answers within 1e-3 of the solver
+    te, dt, per, f_te, sur = trained["te"], trained["dt_te"], trained["p_te"], trained["f_te"], trained["sur"]
+    assert 0.0 < sur.gate(1e-3) <= 1e-3
+    f, fb, t_ans = S.answer(sur, te, dt, per, spread_max=1e-3, batched=True)
+    err = np.abs(f - f_te)
+    rate_sur, rate_batch = len(te) / t_ans, len(te) / trained["t_batch"]
+    acc = ~fb
+    print(f"accepted {acc.mean():.3f} (within 1e-3: {np.mean(err[acc] <= 1e-3):.4f}); all answers within 1e-3: "
+          f"{np.mean(err <= 1e-3):.4f}; surrogate + batched fall-back {rate_sur:.1f} /s, batched alone "
+          f"{rate_batch:.1f} /s")
+    assert acc.mean() > 0.3
+    assert np.mean(err <= 1e-3) >= 0.99
+    assert rate_sur > rate_batch
 
 
 def test_fallback_answers_equal_the_solver(trained):
     te, dt, per, f_te = trained["te"], trained["dt_te"], trained["p_te"], trained["f_te"]
     sur = trained["sur"]
-    assert 0.0 <= sur.gate(1e-3) <= 1e-3       # a spread above the limit always falls back
-    for batched in (False, True):
-        f, fb, _ = S.answer(sur, te, dt, per, spread_max=1e-3, batched=batched)
-        # fall-backs are solver results: single contexts and the batch compute
-        # the same thing (bitwise densities), so they agree to summation order
-        if fb.any():
-            assert np.max(np.abs(f[fb] - f_te[fb])) < 1e-8
-        # accepted answers passed a gate calibrated on held-out training runs;
-        # 1500 training runs give few of them (20000 runs: 10% accepted, 98.6%
-        # of those within 1e-3)
-        acc = ~fb
-        if acc.any():
-            assert np.max(np.abs(f[acc] - f_te[acc])) < 1e-2
+    # a spread above the limit always falls back; one context per fall-back
+    # and the batch compute the same thing (bitwise densities), so the
+    # fall-backs agree with the batch to summation order
+    f, fb, _ = S.answer(sur, te[:40], dt[:40], per[:40], spread_max=1e-3, batched=False)
+    if fb.any():
+        assert np.max(np.abs(f[fb] - f_te[:40][fb])) < 1e-8
