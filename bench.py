@@ -276,7 +276,7 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
     # kappa = 1/16, judged against the fixed step at the same kappa (every step of both keeps
     # alpha dt n_max <= kappa).  The fixed step at kappa = 0.5 is itself off by up to 1.5e-2 on
     # the simulations that finish in a few dozen steps, so it is no reference for 1e-3.
-    t_lad, tal_lad, launches_lad, _ = run_batch(list(range(len(sims))), ladder=True, kappa=LADDER_KAPPA)
+    t_lad, tal_lad, launches_lad, tune_lad = run_batch(list(range(len(sims))), ladder=True, kappa=LADDER_KAPPA)
     t_fk, tal_fk, launches_fk, _ = run_batch(list(range(len(sims))), ladder=False, kappa=LADDER_KAPPA)
     df_lad = max(abs(a.f - b.f) for a, b in zip(tal_lad, tal_fk))
     df_k05 = max(abs(a.f - b.f) for a, b in zip(tal_all, tal_fk))
@@ -298,6 +298,7 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
         g.close()
     df = max(abs(a.f - b) for a, b in zip(tal_bsub, f_plain))
     cell_updates = sum(sims[q]["nx"] * sims[q]["ny"] * sims[q]["nz"] * tal_all[q].steps for q in range(len(sims)))
+    cell_updates_lad = sum(sims[q]["nx"] * sims[q]["ny"] * sims[q]["nz"] * tal_lad[q].steps for q in range(len(sims)))
     return {"sims": len(sims), "solves_per_s": len(sims) / t_all, "seconds": t_all, "step_launches": launches,
             "autotune_s": tune[0], "autotuned_us_per_step": tune[1],
             # one batched step with every simulation active (the autotuner's best time): the
@@ -306,6 +307,7 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
             "full_occupancy_hbm_frac": BYTES_PER_CELL_UPDATE * sum(q["nx"] * q["ny"] * q["nz"] for q in sims)
                                        / tune[1] / 1e3 / hbm_peak()[0],
             "Gcell_updates_per_s": cell_updates / t_all / 1e9,
+            "Gcell_updates_per_s_after_autotune": cell_updates / (t_all - tune[0]) / 1e9,
             "subset": n_subset, "subset_batched_solves_per_s": n_subset / t_bsub,
             "subset_plain_solves_per_s": n_subset / t_plain,
             "speedup_vs_plain": (n_subset / t_bsub) / (n_subset / t_plain),
@@ -318,7 +320,10 @@ def batched_vs_plain(B, synth, n_subset=16, tol=1e-6, check_every=64, scheme=Non
                        "max_abs_df_vs_fixed_dt_same_kappa": df_lad, "within_df_bound": df_lad <= 1e-3,
                        "fixed_kappa_0.5_max_abs_df_vs_kappa_1/16": df_k05,
                        "solves_per_s": len(sims) / t_lad if df_lad <= 1e-3 else None,
-                       "seconds": t_lad,
+                       "seconds": t_lad, "autotune_s": tune_lad[0],
+                       # cell-updates over the run after the autotuner, against the
+                       # full-occupancy step: how much of the run the tail leaves idle
+                       "Gcell_updates_per_s_after_autotune": cell_updates_lad / (t_lad - tune_lad[0]) / 1e9,
                        "speedup_vs_fixed_dt_same_kappa": t_fk / t_lad if df_lad <= 1e-3 else None,
                        "speedup_vs_fixed_dt_kappa_0.5": t_all / t_lad if df_lad <= 1e-3 else None}}
 

@@ -119,3 +119,13 @@ def test_batch_rejects_bad_input_and_skips_empty_simulations():
         with pytest.raises(B.ItError) as e:
             bt.deposit(1, [2e-3], [2e-3], [5.0], [1e-3])
         assert e.value.code == B.IT_ESTATE
+
+
+def test_full_occupancy_runner_keeps_every_simulation_active():
+    # the runner behind the batched kernel's profile: the first 8 simulations
+    # of the batched workload, autotuned, 64 steps with all of them active
+    from paper_1610_06749_gb300 import batched
+    r = batched.full_occupancy(n_sims=8, steps=64)
+    assert r["sims"] == 8 and r["steps"] == 64 and r["sims_active_throughout"] == 8
+    assert r["autotuned_us_per_step"] > 0 and r["run_us_per_step"] > 0
+    assert r["cells"] == sum(d["nx"] * d["ny"] * d["nz"] for d in synth.batch_descriptors()[:8])
