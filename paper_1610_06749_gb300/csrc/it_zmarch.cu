@@ -44,6 +44,7 @@ struct ZmMaps {
 };
 
 constexpr int ZM_MAX_IPT = 4;                    // float4 items per thread
+constexpr int ZM_MAX_SEG = 8;                    // segments of a CTA kept in shared memory
 
 // Persistent step kernel: NW warps, all of them compute.
 //   The planes a CTA needs stream through an S-deep ring of shared-memory
@@ -75,6 +76,7 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     constexpr int WQ = SC ? 16 : 8, NQ = SC ? 9 : 7;
     __shared__ double wacc[NW * WQ];
     __shared__ volatile int abort_flag;
+    __shared__ int seg_n0[ZM_MAX_SEG], seg_t[ZM_MAX_SEG], seg_za[ZM_MAX_SEG];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -86,17 +88,39 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
     const long long g0 = total * blockIdx.x / gridDim.x;
     const long long g1 = total * (blockIdx.x + 1) / gridDim.x;
 
-    // planes this CTA loads: every segment [za, zb) loads zb - za + 2
+    // planes this CTA loads: every segment [za, zb) loads zb - za + 2.  The
+    // first ZM_MAX_SEG segments are also kept in shared memory (first
+    // sequence number, tile, za), so that a refill finds its plane without
+    // the 64-bit divisions of the walk: a refill lies on the critical path,
+    // since the warp that issues it is the last one done with the slot
     int nload = 0;
+    int nseg = 0;
     {
         Segs sg{g0, g1, nz, 0, 0, 0};
-        while (sg.next()) nload += sg.zb - sg.za + 2;
+        while (sg.next()) {
+            if (tid == 0 && nseg < ZM_MAX_SEG) {
+                seg_n0[nseg] = nload;
+                seg_t[nseg] = sg.t;
+                seg_za[nseg] = sg.za;
+            }
+            ++nseg;
+            nload += sg.zb - sg.za + 2;
+        }
     }
+    const bool seg_cached = nseg <= ZM_MAX_SEG;
 
     // load plane n of the sequence into its slot (one thread)
     auto issue = [&](int n) {
         int t = 0, p = 0;
-        if (!plane_of(g0, g1, nz, n, t, p)) return;
+        if (n >= nload) return;
+        if (seg_cached) {
+            int i = 0;
+            while (i + 1 < nseg && n >= seg_n0[i + 1]) ++i;
+            t = seg_t[i];
+            p = seg_za[i] - 1 + (n - seg_n0[i]);
+        } else if (!plane_of(g0, g1, nz, n, t, p)) {
+            return;
+        }
         const int slot = n % S;
         const int y0 = t * zc.TY;
         // halo rows: wrapped when periodic; rows -1 and ny otherwise, which
