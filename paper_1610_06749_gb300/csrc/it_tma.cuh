@@ -157,8 +157,12 @@ __device__ __forceinline__ float4 upd7x4(float4 n, float l, float r, float4 u, f
     const float2 nxy = make_float2(n.x, n.y), nzw = make_float2(n.z, n.w);
     float2 a = __fmul2_rn(WC, nxy);
     float2 b = __fmul2_rn(WC, nzw);
-    a = __ffma2_rn(WX, __fadd2_rn(make_float2(l, n.x), make_float2(n.y, n.z)), a);
-    b = __ffma2_rn(WX, __fadd2_rn(make_float2(n.y, n.z), make_float2(n.w, r)), b);
+    // x neighbours: cell x has (l, y), y has (x, z), z has (y, w), w has (z, r).
+    // These pairs do not sit in aligned register pairs of the float4, so the
+    // four sums are scalar (the same rounding as a paired add) and only the
+    // weighting is paired
+    a = __ffma2_rn(WX, make_float2(__fadd_rn(l, n.y), __fadd_rn(n.x, n.z)), a);
+    b = __ffma2_rn(WX, make_float2(__fadd_rn(n.y, n.w), __fadd_rn(n.z, r)), b);
     a = __ffma2_rn(WY, __fadd2_rn(make_float2(u.x, u.y), make_float2(d.x, d.y)), a);
     b = __ffma2_rn(WY, __fadd2_rn(make_float2(u.z, u.w), make_float2(d.z, d.w)), b);
     a = __ffma2_rn(WZM, make_float2(zm.x, zm.y), a);
