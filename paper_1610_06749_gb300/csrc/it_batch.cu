@@ -315,6 +315,10 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
     __syncthreads();
     const int nx = Sm.nx, ny = Sm.ny, nz = Sm.nz;
     const Coef<float> &c = Sm.cf;
+    // the weights in registers for the march (read from shared memory at
+    // every plane otherwise)
+    const float rwc[2] = {c.wc[0], c.wc[1]}, rwx[2] = {c.wx[0], c.wx[1]}, rwy[2] = {c.wy[0], c.wy[1]};
+    const float rwzm[2] = {c.wzm[0], c.wzm[1]}, rwzp[2] = {c.wzp[0], c.wzp[1]}, radt = c.adt;
     const int ncol4 = nx >> 2;
     const int bt = min(256 / ncol4, ny);           // rows of the main box
     const int rows = E.rows;                        // rows computed (<= bt)
@@ -450,8 +454,8 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
                 if (c4 == 0) l = 0.f;
                 if (c4 == ncol4 - 1) r = 0.f;
             }
-            float4 v = upd7x4(n, l, r, u, d, prev[s], zp, rxy, rzw, c.wc[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s],
-                              c.adt);
+            float4 v = upd7x4(n, l, r, u, d, prev[s], zp, rxy, rzw, rwc[s], rwx[s], rwy[s], rwzm[s], rwzp[s],
+                              radt);
             if (SC) {
                 float2 pxy, pzw;
                 v = add_sc4(v, c.sc[s], n, dxy, dzw, pxy, pzw);
