@@ -78,13 +78,6 @@ static int check_params(const it_params *p, it_grid g, double dx) {
     return IT_OK;
 }
 
-// Round w onto the grid max(q, ulp_T(w)), T having `mant` significand bits.
-static double round_to_grid(double w, double q, int mant) {
-    const double u = w == 0.0 ? q : std::ldexp(1.0, std::ilogb(std::fabs(w)) - (mant - 1));
-    const double g = std::max(q, u);
-    return std::nearbyint(w / g) * g;
-}
-
 template <typename T>
 static void make_coef(Coef<T> &cf, const it_params *p, double dx, double dt) {
     const double E = p->voltage_V / p->gap_cm;
@@ -102,36 +95,12 @@ static void make_coef(Coef<T> &cf, const it_params *p, double dx, double dt) {
             wzm = sd + 0.5 * c * c + 0.5 * sigma * c;
             wzp = sd + 0.5 * c * c - 0.5 * sigma * c;
         }
-        double wx = sd, wy = sd;
-        // increment form of the update, n' = n + [wc n + wx (l + r) + wy (u + d)
-        // + wzm n_{k-1} + wzp n_{k+1} - alpha dt n+ n-]: the centre weight
-        // enters as wc = w0 - 1 = -(2 wx + 2 wy + wzm + wzp), so the five
-        // transport weights of the bracket sum to zero
-        double wc = -(2.0 * wx + 2.0 * wy + wzm + wzp);
-        if (sizeof(T) == 4) {
-            // one common grid q for the FP32 weights, a power of two at 2^-23
-            // of the largest weight: every weight is a multiple of q, so the sum
-            // that gives wc is exact in FP64, and every weight (wc included)
-            // stays below 2^24 q and is exact in FP32.  The bracket's weights
-            // then sum to zero exactly and charge is conserved in real
-            // arithmetic; the grid is 2^-23 of the largest weight (~0.06 at the
-            // workloads' steps), not 2^-23 of w0 ~ 1, so the weights carry 16x
-            // less rounding than a grid set by w0.
-            const double big = std::max({std::fabs(wc), std::fabs(wx), std::fabs(wzm), std::fabs(wzp)});
-            int e = big > 0 ? std::max(std::ilogb(big), -100) : -100;
-            for (;;) {
-                const double q = std::ldexp(1.0, e - 23), lim = std::ldexp(1.0, e + 1);
-                const double rx = round_to_grid(wx, q, 24), ry = round_to_grid(wy, q, 24);
-                const double rzm = round_to_grid(wzm, q, 24), rzp = round_to_grid(wzp, q, 24);
-                const double rc = -(2.0 * rx + 2.0 * ry + rzm + rzp);   // exact in FP64
-                if (std::fabs(rc) < lim && std::fabs(rx) < lim && std::fabs(rzm) < lim && std::fabs(rzp) < lim) {
-                    wx = rx; wy = ry; wzm = rzm; wzp = rzp; wc = rc;
-                    break;
-                }
-                ++e;
-            }
-        }
-        cf.wc[s] = (T)wc;
+        // the update is an increment in flux form (upd7): each transport
+        // weight multiplies a neighbour-minus-cell difference, so the
+        // weights need no common rounding for charge to be conserved and
+        // each is its own nearest value in T; wx = wy because the cells are
+        // cubes, and the x and y terms share one weight in the update
+        const double wx = sd, wy = sd;
         cf.wx[s] = (T)wx;
         cf.wy[s] = (T)wy;
         cf.wzm[s] = (T)wzm;

@@ -88,7 +88,7 @@ step_batched_kernel(const BatchSim *__restrict__ sims, const BatchEntry *__restr
                     const float zm = (k > 0) ? in[idx - plane] : 0.f;
                     const float zp = (k < nz - 1) ? in[idx + plane] : 0.f;
                     float v =
-                        upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.wc[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
+                        upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.wx[s], c.wzm[s], c.wzp[s], c.adt);
                     if constexpr (SC) {
                         v = add_sc(v, c.sc[s], n0, p0, m0);
                         acc[NQ - 2 + s] += (double)__fmul_rn(n0, __fsub_rn(p0, m0));
@@ -206,7 +206,7 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
             float r = __shfl_down_sync(0xffffffffu, n.x, 1);
             if (need_l) l = zero_l ? 0.f : __ldg(in_[s] + pk + row_l);
             if (need_r) r = zero_r ? 0.f : __ldg(in_[s] + pk + row_r);
-            float4 v = upd7x4(n, l, r, u, d, prev[s], nxt[s], rxy, rzw, c.wc[s], c.wx[s], c.wy[s], c.wzm[s],
+            float4 v = upd7x4(n, l, r, u, d, prev[s], nxt[s], rxy, rzw, c.wx[s], c.wzm[s],
                               c.wzp[s], c.adt);
             if (SC) {
                 float2 pxy, pzw;
@@ -317,8 +317,8 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
     const Coef<float> &c = Sm.cf;
     // the weights in registers for the march (read from shared memory at
     // every plane otherwise)
-    const float rwc[2] = {c.wc[0], c.wc[1]}, rwx[2] = {c.wx[0], c.wx[1]}, rwy[2] = {c.wy[0], c.wy[1]};
-    const float rwzm[2] = {c.wzm[0], c.wzm[1]}, rwzp[2] = {c.wzp[0], c.wzp[1]}, radt = c.adt;
+    const float rwx[2] = {c.wx[0], c.wx[1]}, rwzm[2] = {c.wzm[0], c.wzm[1]}, rwzp[2] = {c.wzp[0], c.wzp[1]};
+    const float radt = c.adt;
     const int ncol4 = nx >> 2;
     const int bt = min(256 / ncol4, ny);           // rows of the main box
     const int rows = E.rows;                        // rows computed (<= bt)
@@ -454,7 +454,7 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
                 if (c4 == 0) l = 0.f;
                 if (c4 == ncol4 - 1) r = 0.f;
             }
-            float4 v = upd7x4(n, l, r, u, d, prev[s], zp, rxy, rzw, rwc[s], rwx[s], rwy[s], rwzm[s], rwzp[s],
+            float4 v = upd7x4(n, l, r, u, d, prev[s], zp, rxy, rzw, rwx[s], rwzm[s], rwzp[s],
                               radt);
             if (SC) {
                 float2 pxy, pzw;

@@ -31,31 +31,32 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *smem /* [32][N
     }
 }
 
-// One cell of the update in the increment form of Coef: n + [wc n + wx (l + r)
-// + wy (u + d) + wzm zm + wzp zp - adt rr], the bracket's transport weights
-// summing to zero (wc = w0 - 1).  The bracket's terms are a few percent of n,
-// so their rounding errors are too, and the one rounding of n + bracket is
-// the only one at the scale of n.  The same operation sequence in every
-// kernel, so all kernels round identically.
+// One cell of the update as an increment in flux form:
+//   n + [wd ((l + r) + (u + d) - 4 n) + wzm (zm - n) + wzp (zp - n) - adt rr]
+// (wd = wx = wy: the cells are cubes).  Every transport term is a weight
+// times a neighbour-minus-cell difference, so the transport part of the
+// bracket sums to zero over the grid whatever the rounded weights: charge
+// is moved, never made or lost, and each weight is simply its nearest FP32
+// value.  The bracket's terms are small next to n, so their rounding errors
+// are too; the one rounding of n + bracket is the only one at the scale of
+// n.  The same operation sequence in every kernel, so all kernels round
+// identically.
 __device__ __forceinline__ float upd7(float n, float l, float r, float u, float d, float zm, float zp, float rr,
-                                      float wc, float wx, float wy, float wzm, float wzp, float adt) {
-    float v = __fmul_rn(wc, n);
-    v = __fmaf_rn(wx, __fadd_rn(l, r), v);
-    v = __fmaf_rn(wy, __fadd_rn(u, d), v);
-    v = __fmaf_rn(wzm, zm, v);
-    v = __fmaf_rn(wzp, zp, v);
+                                      float wd, float wzm, float wzp, float adt) {
+    const float s4 = __fadd_rn(__fadd_rn(l, r), __fadd_rn(u, d));
+    float v = __fmul_rn(wd, __fmaf_rn(-4.f, n, s4));
+    v = __fmaf_rn(wzm, __fsub_rn(zm, n), v);
+    v = __fmaf_rn(wzp, __fsub_rn(zp, n), v);
     v = __fmaf_rn(-adt, rr, v);
     return __fadd_rn(n, v);
 }
 
 __device__ __forceinline__ double upd7(double n, double l, double r, double u, double d, double zm, double zp,
-                                       double rr, double wc, double wx, double wy, double wzm, double wzp,
-                                       double adt) {
-    double v = __dmul_rn(wc, n);
-    v = __fma_rn(wx, __dadd_rn(l, r), v);
-    v = __fma_rn(wy, __dadd_rn(u, d), v);
-    v = __fma_rn(wzm, zm, v);
-    v = __fma_rn(wzp, zp, v);
+                                       double rr, double wd, double wzm, double wzp, double adt) {
+    const double s4 = __dadd_rn(__dadd_rn(l, r), __dadd_rn(u, d));
+    double v = __dmul_rn(wd, __fma_rn(-4.0, n, s4));
+    v = __fma_rn(wzm, __dsub_rn(zm, n), v);
+    v = __fma_rn(wzp, __dsub_rn(zp, n), v);
     v = __fma_rn(-adt, rr, v);
     return __dadd_rn(n, v);
 }

@@ -24,17 +24,17 @@ constexpr int NM = 6;
 // finalize output: NT tallies, NM monitor values, released +/-, error flag
 constexpr int NOUT = NT + NM + 3;
 
-// Update weights of one species, in increment form:
-//   n' = n + [wc n + wx (x- + x+) + wy (y- + y+) + wzm z- + wzp z+ - adt n+ n-]
-// with wc = w0 - 1 = -(2wx + 2wy + wzm + wzp); wzm multiplies the neighbour
-// at k-1, wzp the one at k+1.  For FP32 the weights lie on one common grid
-// (2^-23 of the largest weight) so that the bracket's transport weights sum
-// to exactly 0 with every weight exactly representable: the rounded scheme
-// then conserves charge exactly in real arithmetic (only per-operation
-// rounding remains), at a relative perturbation of the weights below 1e-7.
+// Update weights of one species, for the increment in flux form
+//   n' = n + [wx ((x- + x+) + (y- + y+) - 4 n) + wzm (z- - n) + wzp (z+ - n)
+//             - adt n+ n-]
+// (wx = wy: the cells are cubes); wzm multiplies the difference to the
+// neighbour at k-1, wzp the one at k+1.  The transport part sums to zero over
+// the grid for any weights, so each weight is its nearest value in T and
+// charge is conserved in real arithmetic (only per-operation rounding
+// remains).
 template <typename T>
 struct Coef {
-    T wc[2], wx[2], wy[2], wzm[2], wzp[2];   // wc = w0 - 1: the centre weight of the increment form
+    T wx[2], wy[2], wzm[2], wzp[2];
     T adt;            // alpha * dt
     T sc[2];          // space charge: the update adds sc[s] n_s (n+ - n-);
                       // sc = -dt mu+ q/eps0 for n+, +dt mu- q/eps0 for n-
@@ -61,8 +61,10 @@ struct ZmConf {
     int nzc;          // CTAs in the grid (each takes a contiguous range of tile-planes)
     int ntile;        // ny / TY
     int S;            // ring depth (>= 3)
-    int bx;           // TMA box width in x (nx or 256)
+    int bx;           // row width a block holds (nx; 256 for the 3-D maps of nx > 256)
     int nbx;          // nx / bx
+    int xs;           // 1: 3-D maps; nx / 256 > 1: 4-D maps that split a row into xs
+                      // 256-float pieces, so one box carries whole rows (bx = nx)
     int reg_top, reg_main, reg_bot;   // float offsets of the halo/main rows in a block
     int blk;          // floats per (species, x-box) block, 128-byte multiple
     int slot;         // floats per slot = 2 * nbx * blk
@@ -143,8 +145,8 @@ struct it_ctx {
     // z-march kernel configuration (it_zmarch.cu)
     itk::ZmConf zm;
     int zm_grid;
-    CUtensorMap tm_main[2][2];   // [set][species], box {bx, TY, 1}
-    CUtensorMap tm_halo[2][2];   // [set][species], box {bx, 1, 1}
+    CUtensorMap tm_main[2][2];   // [set][species], box {bx, TY, 1} (4-D {256, nx/256, TY, 1} for nx > 256)
+    CUtensorMap tm_halo[2][2];   // [set][species], box {bx, 1, 1} (4-D {256, nx/256, 1, 1} for nx > 256)
     itk::Zm2Conf zm2;            // two steps per launch (IT_KERNEL_ZMARCH2)
     CUtensorMap tm_main2[2][2];  // [set][species], box {bx, TY, 1}
     CUtensorMap tm_halo2[2][2];  // [set][species], box {bx, 2, 1}
@@ -174,6 +176,7 @@ int zmarch_configure(it_ctx *c);
 int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid);
 // FP32 3-D tensor map over [nz][ny][nx] with a box of bx x rows x 1 (it_zmarch.cu)
 int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx, int rows);
+int encode_map_rows(CUtensorMap *m, void *base, int nx, int ny, int nz, int rows);
 int encode_bf16_sw128(CUtensorMap *m, const void *base, long long K, long long rows, long long members,
                       long long row_bytes, long long member_bytes);
 // two steps per launch (it_zmarch2.cu)

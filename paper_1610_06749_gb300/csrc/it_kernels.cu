@@ -52,7 +52,7 @@ step_simple_kernel(const T *__restrict__ ip, const T *__restrict__ im, T *__rest
             const T yp = (PERIODIC || j < ny - 1) ? in[iyp] : T(0);
             const T zm = (k > 0) ? in[idx - plane] : T(0);
             const T zp = (k < nz - 1) ? in[idx + plane] : T(0);
-            T v = upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.wc[s], c.wx[s], c.wy[s], c.wzm[s], c.wzp[s], c.adt);
+            T v = upd7(n0, xm, xp, ym, yp, zm, zp, rr, c.wx[s], c.wzm[s], c.wzp[s], c.adt);
             if (c.sc_on) {
                 v = add_sc(v, c.sc[s], n0, p0, m0);
                 acc[7 + s] += (double)(n0 * (p0 - m0));

@@ -58,6 +58,15 @@ __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, uin
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int xs, int y,
+                                          int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(xs), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // a tensor map read from global memory: order its bytes (written before the
 // launch) before the tensor-map proxy reads them
@@ -146,29 +155,28 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
 }
 
 // Four cells of upd7 (one float4 x-segment) with paired FP32 operations:
-// each lane of a paired operation rounds exactly like the scalar operation,
-// and the sequence is the one of upd7, so the results are bitwise those of
-// the scalar kernels.
+// each lane of a paired operation rounds exactly like the scalar operation
+// (zm - n as fma(-1, n, zm), one rounding like the scalar subtraction), and
+// the sequence is the one of upd7, so the results are bitwise those of the
+// scalar kernels.
 __device__ __forceinline__ float4 upd7x4(float4 n, float l, float r, float4 u, float4 d, float4 zm, float4 zp,
-                                         float2 rxy, float2 rzw, float wc, float wx, float wy, float wzm, float wzp,
-                                         float adt) {
-    const float2 WC = make_float2(wc, wc), WX = make_float2(wx, wx), WY = make_float2(wy, wy);
-    const float2 WZM = make_float2(wzm, wzm), WZP = make_float2(wzp, wzp), NA = make_float2(-adt, -adt);
+                                         float2 rxy, float2 rzw, float wd, float wzm, float wzp, float adt) {
+    const float2 WD = make_float2(wd, wd), WZM = make_float2(wzm, wzm), WZP = make_float2(wzp, wzp);
+    const float2 NA = make_float2(-adt, -adt), M4 = make_float2(-4.f, -4.f), M1 = make_float2(-1.f, -1.f);
     const float2 nxy = make_float2(n.x, n.y), nzw = make_float2(n.z, n.w);
-    float2 a = __fmul2_rn(WC, nxy);
-    float2 b = __fmul2_rn(WC, nzw);
     // x neighbours: cell x has (l, y), y has (x, z), z has (y, w), w has (z, r).
     // These pairs do not sit in aligned register pairs of the float4, so the
-    // four sums are scalar (the same rounding as a paired add) and only the
-    // weighting is paired
-    a = __ffma2_rn(WX, make_float2(__fadd_rn(l, n.y), __fadd_rn(n.x, n.z)), a);
-    b = __ffma2_rn(WX, make_float2(__fadd_rn(n.y, n.w), __fadd_rn(n.z, r)), b);
-    a = __ffma2_rn(WY, __fadd2_rn(make_float2(u.x, u.y), make_float2(d.x, d.y)), a);
-    b = __ffma2_rn(WY, __fadd2_rn(make_float2(u.z, u.w), make_float2(d.z, d.w)), b);
-    a = __ffma2_rn(WZM, make_float2(zm.x, zm.y), a);
-    b = __ffma2_rn(WZM, make_float2(zm.z, zm.w), b);
-    a = __ffma2_rn(WZP, make_float2(zp.x, zp.y), a);
-    b = __ffma2_rn(WZP, make_float2(zp.z, zp.w), b);
+    // four sums are scalar (the same rounding as a paired add)
+    const float2 xa = make_float2(__fadd_rn(l, n.y), __fadd_rn(n.x, n.z));
+    const float2 xb = make_float2(__fadd_rn(n.y, n.w), __fadd_rn(n.z, r));
+    const float2 sa = __fadd2_rn(xa, __fadd2_rn(make_float2(u.x, u.y), make_float2(d.x, d.y)));
+    const float2 sb = __fadd2_rn(xb, __fadd2_rn(make_float2(u.z, u.w), make_float2(d.z, d.w)));
+    float2 a = __fmul2_rn(WD, __ffma2_rn(M4, nxy, sa));
+    float2 b = __fmul2_rn(WD, __ffma2_rn(M4, nzw, sb));
+    a = __ffma2_rn(WZM, __ffma2_rn(M1, nxy, make_float2(zm.x, zm.y)), a);
+    b = __ffma2_rn(WZM, __ffma2_rn(M1, nzw, make_float2(zm.z, zm.w)), b);
+    a = __ffma2_rn(WZP, __ffma2_rn(M1, nxy, make_float2(zp.x, zp.y)), a);
+    b = __ffma2_rn(WZP, __ffma2_rn(M1, nzw, make_float2(zp.z, zp.w)), b);
     a = __ffma2_rn(NA, rxy, a);
     b = __ffma2_rn(NA, rzw, b);
     a = __fadd2_rn(nxy, a);

@@ -134,6 +134,14 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, tx);
         for (int s = 0; s < 2; ++s) {
+            if (zc.xs > 1) {
+                // whole rows of a wide grid in one box (nbx == 1)
+                float *blk = base + (size_t)s * zc.blk;
+                tma_load4(blk + zc.reg_main, &maps.main[s], bar, 0, 0, y0, p);
+                tma_load4(blk + zc.reg_top, &maps.halo[s], bar, 0, 0, ytop, p);
+                tma_load4(blk + zc.reg_bot, &maps.halo[s], bar, 0, 0, ybot, p);
+                continue;
+            }
             for (int b = 0; b < zc.nbx; ++b) {
                 float *blk = base + (size_t)(s * zc.nbx + b) * zc.blk;
                 tma_load3(blk + zc.reg_main, &maps.main[s], bar, b * zc.bx, y0, p);
@@ -290,8 +298,8 @@ step_zmarch_kernel(const __grid_constant__ ZmMaps maps, float *__restrict__ outp
                         if (c4_[it] == 0) l = 0.f;
                         if (c4_[it] == ncol4 - 1) r = 0.f;
                     }
-                    float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw, cf.wc[s], cf.wx[s], cf.wy[s],
-                                      cf.wzm[s], cf.wzp[s], cf.adt);
+                    float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw,
+                                      cf.wx[s], cf.wzm[s], cf.wzp[s], cf.adt);
                     if (SC) {
                         float2 pxy, pzw;
                         v = add_sc4(v, cf.sc[s], n, dxy, dzw, pxy, pzw);
@@ -406,6 +414,31 @@ int encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, int bx, int r
     return IT_OK;
 }
 
+// Wide rows (nx > 256, nx % 256 == 0): a 4-D view {256, nx / 256, ny, nz} of
+// the same array (byte strides 1 KiB, one row, one plane), boxes of
+// {256, nx / 256, rows, 1}, which land in shared memory as `rows` whole rows
+// of nx floats: one copy per box where the 3-D view needs nx / 256.
+int encode_map_rows(CUtensorMap *m, void *base, int nx, int ny, int nz, int rows) {
+    auto fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available");
+        return IT_ECUDA;
+    }
+    const int xs = nx / 256;
+    cuuint64_t dims[4] = {256, (cuuint64_t)xs, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t strides[3] = {256 * 4, (cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    cuuint32_t box[4] = {256, (cuuint32_t)xs, (cuuint32_t)rows, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled (row view) failed (code " + std::to_string((int)r) + ")");
+        return IT_ECUDA;
+    }
+    return IT_OK;
+}
+
 // bf16 operand of the tensor-core GEMM (it_tc.cuh): dims {K, rows, members}
 // (K contiguous), byte strides of a row and of a member, boxes of 64 x 128
 // with the 128-byte swizzle; rows and K beyond the dims arrive as zeros.
@@ -477,8 +510,11 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid
     const int nw = cps == 1 ? 16 : 8;
     ZmConf z{};
     z.threads = nw * 32;
-    z.bx = nx <= 256 ? nx : 256;
-    z.nbx = nx / z.bx;
+    // a ring block holds whole rows; rows wider than a TMA box dimension (256
+    // floats) come through the 4-D view (nx / 256 pieces per row, one box)
+    z.xs = nx > 256 ? nx / 256 : 1;
+    z.bx = nx;
+    z.nbx = 1;
     // rows per tile: the smallest divisor of ny that gives every thread two
     // float4 items (else the largest with at most ZM_MAX_IPT)
     int TY = want_ty;
@@ -547,9 +583,11 @@ int zmarch_setup(it_ctx *c, int want_ty, int want_cps, int want_s, int want_grid
     z.nzc = (int)std::min<long long>(grid, tp);
     for (int set = 0; set < 2; ++set)
         for (int s = 0; s < 2; ++s) {
-            int rc = encode_map(&c->tm_main[set][s], c->n[set][s], nx, ny, nz, z.bx, TY);
+            int rc = z.xs > 1 ? encode_map_rows(&c->tm_main[set][s], c->n[set][s], nx, ny, nz, TY)
+                              : encode_map(&c->tm_main[set][s], c->n[set][s], nx, ny, nz, z.bx, TY);
             if (rc) return rc;
-            rc = encode_map(&c->tm_halo[set][s], c->n[set][s], nx, ny, nz, z.bx, 1);
+            rc = z.xs > 1 ? encode_map_rows(&c->tm_halo[set][s], c->n[set][s], nx, ny, nz, 1)
+                          : encode_map(&c->tm_halo[set][s], c->n[set][s], nx, ny, nz, z.bx, 1);
             if (rc) return rc;
         }
     c->zm = z;

@@ -251,8 +251,7 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
                     float l = bk[t_l], r = bk[t_r];
                     if (zero_l) l = 0.f;
                     if (zero_r) r = 0.f;
-                    float4 v = upd7x4(Tc[s], l, r, u, d, Tp[s], zp, rxy, rzw, cf.wc[s], cf.wx[s], cf.wy[s],
-                                      cf.wzm[s], cf.wzp[s], cf.adt);
+                    float4 v = upd7x4(Tc[s], l, r, u, d, Tp[s], zp, rxy, rzw, cf.wx[s], cf.wzm[s], cf.wzp[s], cf.adt);
                     if (SC) {
                         float2 pxy, pzw;
                         v = add_sc4(v, cf.sc[s], Tc[s], dxy, dzw, pxy, pzw);
@@ -287,8 +286,7 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
                     float l = bk[h_l], r = bk[h_r];
                     if (hzero_l) l = 0.f;
                     if (hzero_r) r = 0.f;
-                    float4 v = upd7x4(Hc[s], l, r, u, d, Hp[s], zp, rxy, rzw, cf.wc[s], cf.wx[s], cf.wy[s],
-                                      cf.wzm[s], cf.wzp[s], cf.adt);
+                    float4 v = upd7x4(Hc[s], l, r, u, d, Hp[s], zp, rxy, rzw, cf.wx[s], cf.wzm[s], cf.wzp[s], cf.adt);
                     if (SC) {
                         float2 pxy, pzw;
                         v = add_sc4(v, cf.sc[s], Hc[s], dxy, dzw, pxy, pzw);   // halo: not tallied
@@ -328,8 +326,8 @@ step_zmarch2_kernel(const __grid_constant__ Zm2Maps maps, float *__restrict__ ou
                     float l = bk[m_l], r = bk[m_r];
                     if (zero_l) l = 0.f;
                     if (zero_r) r = 0.f;
-                    float4 v = upd7x4(Mm1[s], l, r, u, d, Mm2[s], Mj[s], rxy, rzw, cf.wc[s], cf.wx[s],
-                                      cf.wy[s], cf.wzm[s], cf.wzp[s], cf.adt);
+                    float4 v = upd7x4(Mm1[s], l, r, u, d, Mm2[s], Mj[s], rxy, rzw,
+                                      cf.wx[s], cf.wzm[s], cf.wzp[s], cf.adt);
                     if (SC) {
                         float2 pxy, pzw;
                         v = add_sc4(v, cf.sc[s], Mm1[s], dxy, dzw, pxy, pzw);

@@ -1,10 +1,10 @@
 """What FP32 arithmetic alone does to the scheme (no GPU): the reason for the
 pointwise density tolerance of the Lax-Wendroff parity tests.
 
-A plain float32 evaluation of the Appendix update in the increment form the
-CUDA kernels use, n + [wc n + wx (left + right) + wy (down + up) +
-wz- n_{k-1} + wz+ n_{k+1} - alpha dt n+ n-] with wc = -(2 wx + 2 wy + wz- +
-wz+) (written out here with numpy, every operation rounded to float32), is
+A plain float32 evaluation of the Appendix update in the flux form the CUDA
+kernels use, n + [wd ((left + right) + (down + up) - 4 n) + wz- (n_{k-1} - n)
++ wz+ (n_{k+1} - n) - alpha dt n+ n-] (written out here with numpy, every
+operation rounded to float32, the weights their nearest float32 values), is
 compared with the FP64 oracle from the same deposited state.
 
 * Upwind drift has non-negative weights: every cell is a convex combination
@@ -47,23 +47,27 @@ def _weights(dx, dt, E, upwind):
 
 
 def _float32_steps(p, m, w, adt, n):
-    """n steps in the increment form, periodic x/y faces, zero ghost planes
-    at the electrodes."""
-    p, m = p.astype(np.float32), m.astype(np.float32)
-    adt = np.float32(adt)
+    """n steps of the flux form, periodic x/y faces, zero ghost planes at the
+    electrodes; fused multiply-adds rounded once (through float64)."""
+    f32, f64 = np.float32, np.float64
+    p, m = p.astype(f32), m.astype(f32)
     for _ in range(n):
-        r = (adt * p) * m
+        r = (p * m).astype(f32)
         new = []
         for s, a in enumerate((p, m)):
-            _, wx, wy, wzm, wzp = w[s]
-            wc = np.float32(-(2.0 * float(wx) + 2.0 * float(wy) + float(wzm) + float(wzp)))
+            _, wd, _, wzm, wzp = w[s]
             below = np.zeros_like(a)
             below[1:] = a[:-1]
             above = np.zeros_like(a)
             above[:-1] = a[1:]
-            v = wc * a + wx * (np.roll(a, 1, 2) + np.roll(a, -1, 2)) + wy * (np.roll(a, 1, 1) + np.roll(a, -1, 1))
-            v = v + wzm * below + wzp * above - r
-            new.append((a + v).astype(np.float32))
+            s4 = ((np.roll(a, 1, 2) + np.roll(a, -1, 2)).astype(f32)
+                  + (np.roll(a, 1, 1) + np.roll(a, -1, 1)).astype(f32)).astype(f32)
+            dif = (s4.astype(f64) - 4.0 * a.astype(f64)).astype(f32)
+            v = (f64(wd) * dif.astype(f64)).astype(f32)
+            v = (f64(wzm) * (below - a).astype(f32).astype(f64) + v.astype(f64)).astype(f32)
+            v = (f64(wzp) * (above - a).astype(f32).astype(f64) + v.astype(f64)).astype(f32)
+            v = (-f64(np.float32(adt)) * r.astype(f64) + v.astype(f64)).astype(f32)
+            new.append((a + v).astype(f32))
         p, m = new
     return p, m
 

@@ -87,6 +87,9 @@ CASES = [
     (64, 48, 40, 4e-4, 100.0, B.IT_ABSORBING, B.IT_UPWIND, B.IT_KERNEL_ZMARCH, 25),
     (256, 16, 12, 5e-4, 300.0, B.IT_PERIODIC, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH, 40),
     (512, 8, 10, 5e-4, 300.0, B.IT_ABSORBING, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH, 40),
+    # rows wider than a TMA box: whole rows through the 4-D view, periodic wrap
+    (512, 8, 10, 5e-4, 300.0, B.IT_PERIODIC, B.IT_UPWIND, B.IT_KERNEL_ZMARCH, 40),
+    (768, 4, 12, 5e-4, 200.0, B.IT_PERIODIC, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH, 30),
     # two steps per launch (odd step counts end on the simple kernel)
     (64, 48, 40, 4e-4, 100.0, B.IT_PERIODIC, B.IT_LAX_WENDROFF, B.IT_KERNEL_ZMARCH2, 25),
     (64, 48, 40, 4e-4, 100.0, B.IT_ABSORBING, B.IT_UPWIND, B.IT_KERNEL_ZMARCH2, 25),
