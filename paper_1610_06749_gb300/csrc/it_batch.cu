@@ -288,11 +288,17 @@ constexpr int BT_WARPS = 8;
 // ring gets whatever slots fit (3..8; a slot is at most 12 KiB at nx = 256)
 constexpr int kBtSmem = 70 * 1024;
 constexpr int kBtSmemFloats = (kBtSmem - 128) / 4;
+// with two float4 per thread: two CTAs per SM, twice the rows per box
+constexpr int kBtSmem2 = 105 * 1024;
+constexpr int kBtSmemFloats2 = (kBtSmem2 - 128) / 4;
+// tensor maps per simulation: [set][species][main box of one float4 per
+// thread, main box of two, halo row]
+constexpr int BT_MAPS = 12;
 
 __device__ __forceinline__ int bt_align32(int f) { return (f + 31) & ~31; }
 
-template <bool PERIODIC, bool SC>
-__global__ void __launch_bounds__(BT_WARPS * 32, 3)
+template <bool PERIODIC, bool SC, int IPT>
+__global__ void __launch_bounds__(BT_WARPS * 32, (IPT == 1 ? 3 : 2))
 step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__restrict__ tab,
                         const CUtensorMap *__restrict__ maps, int parity, float *__restrict__ op_all,
                         float *__restrict__ om_all, double *__restrict__ slots, int smem_floats,
@@ -320,12 +326,12 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
     const float rwx[2] = {c.wx[0], c.wx[1]}, rwzm[2] = {c.wzm[0], c.wzm[1]}, rwzp[2] = {c.wzp[0], c.wzp[1]};
     const float radt = c.adt;
     const int ncol4 = nx >> 2;
-    const int bt = min(256 / ncol4, ny);           // rows of the main box
+    const int bt = min(min(256 * IPT / ncol4, 256), ny);   // rows of the main box (a box dimension is <= 256)
     const int rows = E.rows;                        // rows computed (<= bt)
     const int reg_main = bt_align32(nx), reg_bot = reg_main + bt_align32(bt * nx), blk = reg_bot + bt_align32(nx);
     const int slotf = 2 * blk;
     const int S = min(smem_floats / slotf, BT_MAX_S);   // the host keeps this >= 3
-    const CUtensorMap *mp = maps + (size_t)E.sim * 8 + parity * 4;   // [species][main, halo]
+    const CUtensorMap *mp = maps + (size_t)E.sim * BT_MAPS + parity * 6;   // [species][main1, main2, halo]
     const int z0 = E.z0, z1 = E.z1, y0 = E.y0;
     const int nload = z1 - z0 + 2;                  // planes z0 - 1 .. z1
     const int ytop = PERIODIC ? (y0 > 0 ? y0 - 1 : ny - 1) : y0 - 1;
@@ -342,15 +348,15 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         mbar_arrive_expect_tx(bar, tx);
         for (int s = 0; s < 2; ++s) {
             float *b = base + s * blk;
-            tma_load3(b + reg_main, &mp[2 * s], bar, 0, y0, p);
-            tma_load3(b, &mp[2 * s + 1], bar, 0, ytop, p);
-            tma_load3(b + reg_bot, &mp[2 * s + 1], bar, 0, ybot, p);
+            tma_load3(b + reg_main, &mp[3 * s + IPT - 1], bar, 0, y0, p);
+            tma_load3(b, &mp[3 * s + 2], bar, 0, ytop, p);
+            tma_load3(b + reg_bot, &mp[3 * s + 2], bar, 0, ybot, p);
         }
         fills[slot] += 1;
     };
 
     if (tid == 0) {
-        for (int q = 0; q < 4; ++q) fence_tensormap_acquire(&mp[q]);
+        for (int q = 0; q < 6; ++q) fence_tensormap_acquire(&mp[q]);
         for (int q = 0; q < S; ++q) {
             mbar_init(&full[q], 1);
             rel[q] = 0;
@@ -370,22 +376,31 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         if (lane == 0) wacc[warp * WQ + q] += v;
     };
 
-    // this thread's float4 segment; threads past the tile repeat its last
-    // row's segment and store nothing
-    const bool valid = tid < rows * ncol4;
-    const int te = valid ? tid : rows * ncol4 - 1;
-    const int ty = te / ncol4, c4 = te - ty * ncol4;
-    const int x0 = 4 * c4;
-    const int o_c = reg_main + ty * nx + x0;
-    const int o_u = ty == 0 ? x0 : reg_main + (ty - 1) * nx + x0;
-    const int o_d = ty == rows - 1 ? reg_bot + x0 : reg_main + (ty + 1) * nx + x0;
-    const int o_l = reg_main + ty * nx + (c4 == 0 ? nx - 1 : x0 - 1);
-    const int o_r = reg_main + ty * nx + (c4 == ncol4 - 1 ? 0 : x0 + 4);
-    const int yg = y0 + ty;
-    const bool edge_u = !PERIODIC && yg == 0, edge_d = !PERIODIC && yg == ny - 1;
-    float *out_[2] = {op_all + Sm.off, om_all + Sm.off};
+    // this thread's float4 segments q = tid + 256 it; threads past the tile
+    // repeat its last segment and store nothing
+    bool valid[IPT], edge_u[IPT], edge_d[IPT];
+    int c4_[IPT], o_c[IPT], o_u[IPT], o_d[IPT], o_l[IPT], o_r[IPT];
+    uint32_t off[IPT];
     const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
-    uint32_t off = ((uint32_t)z0 * (uint32_t)ny + (uint32_t)yg) * (uint32_t)nx + (uint32_t)x0;
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+        const int q = tid + it * BT_WARPS * 32;
+        valid[it] = q < rows * ncol4;
+        const int te = valid[it] ? q : rows * ncol4 - 1;
+        const int ty = te / ncol4, c4 = te - ty * ncol4;
+        const int x0 = 4 * c4;
+        c4_[it] = c4;
+        o_c[it] = reg_main + ty * nx + x0;
+        o_u[it] = ty == 0 ? x0 : reg_main + (ty - 1) * nx + x0;
+        o_d[it] = ty == rows - 1 ? reg_bot + x0 : reg_main + (ty + 1) * nx + x0;
+        o_l[it] = reg_main + ty * nx + (c4 == 0 ? nx - 1 : x0 - 1);
+        o_r[it] = reg_main + ty * nx + (c4 == ncol4 - 1 ? 0 : x0 + 4);
+        const int yg = y0 + ty;
+        edge_u[it] = !PERIODIC && yg == 0;
+        edge_d[it] = !PERIODIC && yg == ny - 1;
+        off[it] = ((uint32_t)z0 * (uint32_t)ny + (uint32_t)yg) * (uint32_t)nx + (uint32_t)x0;
+    }
+    float *out_[2] = {op_all + Sm.off, om_all + Sm.off};
 
     RingPos pos{0, 0u};
     int nrel = 0;
@@ -412,12 +427,15 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         ++nrel;
     };
 
-    float4 prev[2], cur[2];
+    float4 prev[IPT][2], cur[IPT][2];
     wait_full(pos);
     {
         const float *sl = ring + (size_t)pos.slot * slotf;
-        prev[0] = *reinterpret_cast<const float4 *>(sl + o_c);
-        prev[1] = *reinterpret_cast<const float4 *>(sl + blk + o_c);
+#pragma unroll
+        for (int it = 0; it < IPT; ++it) {
+            prev[it][0] = *reinterpret_cast<const float4 *>(sl + o_c[it]);
+            prev[it][1] = *reinterpret_cast<const float4 *>(sl + blk + o_c[it]);
+        }
     }
     release(pos);
     pos.advance(S);
@@ -426,8 +444,11 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
     pos.advance(S);
     {
         const float *sl = ring + (size_t)pc.slot * slotf;
-        cur[0] = *reinterpret_cast<const float4 *>(sl + o_c);
-        cur[1] = *reinterpret_cast<const float4 *>(sl + blk + o_c);
+#pragma unroll
+        for (int it = 0; it < IPT; ++it) {
+            cur[it][0] = *reinterpret_cast<const float4 *>(sl + o_c[it]);
+            cur[it][1] = *reinterpret_cast<const float4 *>(sl + blk + o_c[it]);
+        }
     }
     float rsum = 0.f, lsum0 = 0.f, lsum1 = 0.f, ssum0 = 0.f, ssum1 = 0.f;
     int nacc = 0;
@@ -436,46 +457,48 @@ step_batched_tma_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
         const float *sk = ring + (size_t)pc.slot * slotf;
         const float *sn = ring + (size_t)pos.slot * slotf;
         float an[2] = {0.f, 0.f}, lat[2] = {0.f, 0.f};
-        const float4 P = cur[0], M = cur[1];
-        const float2 rxy = __fmul2_rn(make_float2(P.x, P.y), make_float2(M.x, M.y));
-        const float2 rzw = __fmul2_rn(make_float2(P.z, P.w), make_float2(M.z, M.w));
-        float2 dxy, dzw;
-        if (SC) sc_diff4(P, M, dxy, dzw);
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const float *bk = sk + s * blk;
-            const float4 n = cur[s];
-            const float4 u = *reinterpret_cast<const float4 *>(bk + o_u);
-            const float4 d = *reinterpret_cast<const float4 *>(bk + o_d);
-            const float4 zp = *reinterpret_cast<const float4 *>(sn + s * blk + o_c);
-            float l = bk[o_l];
-            float r = bk[o_r];
-            if (!PERIODIC) {
-                if (c4 == 0) l = 0.f;
-                if (c4 == ncol4 - 1) r = 0.f;
-            }
-            float4 v = upd7x4(n, l, r, u, d, prev[s], zp, rxy, rzw, rwx[s], rwzm[s], rwzp[s],
-                              radt);
-            if (SC) {
-                float2 pxy, pzw;
-                v = add_sc4(v, c.sc[s], n, dxy, dzw, pxy, pzw);
-                if (valid) (s ? ssum1 : ssum0) += (pxy.x + pxy.y) + (pzw.x + pzw.y);
-            }
-            if (valid) {
-                *reinterpret_cast<float4 *>(out_[s] + off) = v;
-                if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
+        for (int it = 0; it < IPT; ++it) {
+            const float4 P = cur[it][0], M = cur[it][1];
+            const float2 rxy = __fmul2_rn(make_float2(P.x, P.y), make_float2(M.x, M.y));
+            const float2 rzw = __fmul2_rn(make_float2(P.z, P.w), make_float2(M.z, M.w));
+            float2 dxy, dzw;
+            if (SC) sc_diff4(P, M, dxy, dzw);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float *bk = sk + s * blk;
+                const float4 n = cur[it][s];
+                const float4 u = *reinterpret_cast<const float4 *>(bk + o_u[it]);
+                const float4 d = *reinterpret_cast<const float4 *>(bk + o_d[it]);
+                const float4 zp = *reinterpret_cast<const float4 *>(sn + s * blk + o_c[it]);
+                float l = bk[o_l[it]];
+                float r = bk[o_r[it]];
                 if (!PERIODIC) {
-                    if (c4 == 0) lat[s] += n.x;
-                    if (c4 == ncol4 - 1) lat[s] += n.w;
-                    if (edge_u) lat[s] += (n.x + n.y) + (n.z + n.w);
-                    if (edge_d) lat[s] += (n.x + n.y) + (n.z + n.w);
+                    if (c4_[it] == 0) l = 0.f;
+                    if (c4_[it] == ncol4 - 1) r = 0.f;
                 }
+                float4 v = upd7x4(n, l, r, u, d, prev[it][s], zp, rxy, rzw, rwx[s], rwzm[s], rwzp[s], radt);
+                if (SC) {
+                    float2 pxy, pzw;
+                    v = add_sc4(v, c.sc[s], n, dxy, dzw, pxy, pzw);
+                    if (valid[it]) (s ? ssum1 : ssum0) += (pxy.x + pxy.y) + (pzw.x + pzw.y);
+                }
+                if (valid[it]) {
+                    *reinterpret_cast<float4 *>(out_[s] + off[it]) = v;
+                    if (k == 0 || k == nz - 1) an[s] += (n.x + n.y) + (n.z + n.w);
+                    if (!PERIODIC) {
+                        if (c4_[it] == 0) lat[s] += n.x;
+                        if (c4_[it] == ncol4 - 1) lat[s] += n.w;
+                        if (edge_u[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
+                        if (edge_d[it]) lat[s] += (n.x + n.y) + (n.z + n.w);
+                    }
+                }
+                prev[it][s] = n;
+                cur[it][s] = zp;
             }
-            prev[s] = n;
-            cur[s] = zp;
+            if (valid[it]) rsum += (rxy.x + rxy.y) + (rzw.x + rzw.y);
+            off[it] += plane;
         }
-        if (valid) rsum += (rxy.x + rxy.y) + (rzw.x + rzw.y);
-        off += plane;
         if (!PERIODIC) { lsum0 += lat[0]; lsum1 += lat[1]; }
         if (++nacc == 32) {
             flush(0, rsum);
@@ -645,6 +668,7 @@ struct it_batch {
     CUtensorMap *d_maps;
     std::vector<char> tma_ok;
     int use_tma;
+    int tma_ipt;                      // float4 per thread of the TMA kernel (1 or 2)
     int nvt;
     int *d_err;
 };
@@ -698,7 +722,10 @@ int build_table(it_batch *b) {
         b->mcount.push_back(n);
         b->morder.push_back(s);
         if (h.nx % 4 == 0 && h.nx <= 1024) {
-            const int rpt = std::max(1, 256 / (h.nx / 4));
+            // rows per entry: a 256-thread tile of float4 (times the TMA
+            // kernel's float4 per thread for the simulations it takes)
+            const int ipt = (b->use_tma && b->tma_ok[s]) ? b->tma_ipt : 1;
+            const int rpt = std::max(1, std::min(256 * ipt / (h.nx / 4), 256));
             const int zc = (int)std::min<long long>(zsplit, std::max(1, h.nz / 8));
             vsim.push_back(s);
             vfirst.push_back((int)b->vtab.size());
@@ -771,10 +798,14 @@ int launch_batched_step(it_batch *b, int parity) {
     const bool per = b->p.lateral_bc == IT_PERIODIC;
     const bool sc = b->p.space_charge != 0;
     if (nt) {
-        auto *kt = per ? (sc ? step_batched_tma_kernel<true, true> : step_batched_tma_kernel<true, false>)
-                       : (sc ? step_batched_tma_kernel<false, true> : step_batched_tma_kernel<false, false>);
-        kt<<<nt, BT_WARPS * 32, kBtSmem, b->stream>>>(b->d_sims, b->d_vtab, b->d_maps, parity, op, om, b->d_slots,
-                                                     kBtSmemFloats, b->d_err);
+        const bool two = b->tma_ipt == 2;
+        auto *kt = two ? (per ? (sc ? step_batched_tma_kernel<true, true, 2> : step_batched_tma_kernel<true, false, 2>)
+                              : (sc ? step_batched_tma_kernel<false, true, 2> : step_batched_tma_kernel<false, false, 2>))
+                       : (per ? (sc ? step_batched_tma_kernel<true, true, 1> : step_batched_tma_kernel<true, false, 1>)
+                              : (sc ? step_batched_tma_kernel<false, true, 1> : step_batched_tma_kernel<false, false, 1>));
+        kt<<<nt, BT_WARPS * 32, two ? kBtSmem2 : kBtSmem, b->stream>>>(b->d_sims, b->d_vtab, b->d_maps, parity, op,
+                                                                       om, b->d_slots,
+                                                                       two ? kBtSmemFloats2 : kBtSmemFloats, b->d_err);
         IT_CK(cudaGetLastError());
     }
     if (nv > nt) {
@@ -1003,24 +1034,27 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
         (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
         return bail(e, "batch setup");
     // tensor maps of the TMA batched kernel: simulations with nx % 4 == 0 and
-    // nx <= 256 (one box spans the row); boxes of min(256 / (nx/4), ny) rows
-    // and of one halo row
+    // nx <= 256 (one box spans the row); main boxes of min(256 / (nx/4), ny)
+    // and min(512 / (nx/4), ny) rows (one or two float4 per thread) and a
+    // box of one halo row
     b->tma_ok.assign(nsim, 0);
     b->use_tma = 1;
+    b->tma_ipt = 1;
     {
-        std::vector<CUtensorMap> maps((size_t)nsim * 8);
+        std::vector<CUtensorMap> maps((size_t)nsim * BT_MAPS);
         std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
         for (int s = 0; s < nsim; ++s) {
             const BatchSim &h = b->hs[s];
             if (h.nx % 4 != 0 || h.nx > 256) continue;
-            const int rows = std::min(256 / (h.nx / 4), h.ny);
             int rc = IT_OK;
             for (int set = 0; set < 2 && rc == IT_OK; ++set)
                 for (int sp = 0; sp < 2 && rc == IT_OK; ++sp) {
                     float *base_s = b->state[set][sp] + h.off;
-                    rc = encode_map(&maps[(size_t)s * 8 + set * 4 + sp * 2], base_s, h.nx, h.ny, h.nz, h.nx, rows);
-                    if (rc == IT_OK)
-                        rc = encode_map(&maps[(size_t)s * 8 + set * 4 + sp * 2 + 1], base_s, h.nx, h.ny, h.nz, h.nx, 1);
+                    CUtensorMap *m = &maps[(size_t)s * BT_MAPS + set * 6 + sp * 3];
+                    for (int ipt = 1; ipt <= 2 && rc == IT_OK; ++ipt)
+                        rc = encode_map(&m[ipt - 1], base_s, h.nx, h.ny, h.nz, h.nx,
+                                        std::min(std::min(256 * ipt / (h.nx / 4), 256), h.ny));
+                    if (rc == IT_OK) rc = encode_map(&m[2], base_s, h.nx, h.ny, h.nz, h.nx, 1);
                 }
             if (rc) { batch_free(b); return rc; }
             b->tma_ok[s] = 1;
@@ -1032,9 +1066,13 @@ int it_batch_create(int32_t nsim, const it_sim_desc *descs, const it_params *com
             (e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
             return bail(e, "batch tensor maps");
-        for (auto *k : {step_batched_tma_kernel<true, true>, step_batched_tma_kernel<true, false>,
-                        step_batched_tma_kernel<false, true>, step_batched_tma_kernel<false, false>})
+        for (auto *k : {step_batched_tma_kernel<true, true, 1>, step_batched_tma_kernel<true, false, 1>,
+                        step_batched_tma_kernel<false, true, 1>, step_batched_tma_kernel<false, false, 1>})
             if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kBtSmem)) != cudaSuccess)
+                return bail(e, "cudaFuncSetAttribute(batched TMA kernel)");
+        for (auto *k : {step_batched_tma_kernel<true, true, 2>, step_batched_tma_kernel<true, false, 2>,
+                        step_batched_tma_kernel<false, true, 2>, step_batched_tma_kernel<false, false, 2>})
+            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kBtSmem2)) != cudaSuccess)
                 return bail(e, "cudaFuncSetAttribute(batched TMA kernel)");
     }
     b->tab_dirty = true;
@@ -1194,15 +1232,18 @@ int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us) {
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         rc = cuda_fail(cudaGetLastError(), "batch autotune set-up");
     const long long chunk0 = b->chunk;
-    const int cps0 = b->vec_cps, tma0 = b->use_tma;
+    // TMA choice: 2 = the TMA kernel with two float4 per thread, 1 = with
+    // one, 0 = the register kernel
+    const int cps0 = b->vec_cps, tma0 = b->use_tma ? b->tma_ipt : 0;
     long long best_chunk = chunk0;
     int best_cps = cps0, best_tma = tma0;
     double best = 1e300;
-    for (int tma : {1, 0})
+    for (int tma : {2, 1, 0})
     for (int cps : {1, 2, 4, 8, 16, 32}) {
         for (long long chunk : {4096LL, 16384LL, 65536LL}) {
             if (rc) break;
-            b->use_tma = tma;
+            b->use_tma = tma > 0;
+            b->tma_ipt = tma == 2 ? 2 : 1;
             b->vec_cps = cps;
             b->chunk = chunk;
             rc = build_table(b);
@@ -1235,7 +1276,9 @@ int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us) {
     // the chosen shape; the next table build also clears the trial tallies
     b->chunk = rc ? chunk0 : best_chunk;
     b->vec_cps = rc ? cps0 : best_cps;
-    b->use_tma = rc ? tma0 : best_tma;
+    const int tma_sel = rc ? tma0 : best_tma;
+    b->use_tma = tma_sel > 0;
+    b->tma_ipt = tma_sel == 2 ? 2 : 1;
     b->tab_dirty = true;
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     if (rc) return rc;
