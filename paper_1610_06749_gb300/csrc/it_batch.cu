@@ -1238,9 +1238,16 @@ int it_batch_autotune(it_batch *b, int32_t trial_steps, double *best_us) {
     long long best_chunk = chunk0;
     int best_cps = cps0, best_tma = tma0;
     double best = 1e300;
+    // the entry size only shapes the scalar kernel's entries: with no
+    // simulation on that kernel a single size is timed
+    bool any_scalar = false;
+    for (int s = 0; s < b->nsim; ++s)
+        if (b->active[s] && !(b->hs[s].nx % 4 == 0 && b->hs[s].nx <= 1024)) any_scalar = true;
+    const std::vector<long long> chunks = any_scalar ? std::vector<long long>{4096LL, 16384LL, 65536LL}
+                                                     : std::vector<long long>{chunk0};
     for (int tma : {2, 1, 0})
     for (int cps : {1, 2, 4, 8, 16, 32}) {
-        for (long long chunk : {4096LL, 16384LL, 65536LL}) {
+        for (long long chunk : chunks) {
             if (rc) break;
             b->use_tma = tma > 0;
             b->tma_ipt = tma == 2 ? 2 : 1;
