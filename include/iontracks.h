@@ -401,8 +401,10 @@ int it_batch_set_chunk(it_batch *b, int64_t cells_per_block);
 /* Native autotuner of the batched launch shape: after the deposits (and
  * it_batch_retime), before the first step.  Times trial_steps (>= 2, rounded
  * up to even) batched steps of the deposited state for each candidate --
- * float4-kernel z splits aiming at 1..32 CTAs per SM, times 4096 / 16384 /
- * 65536 cells per scalar-kernel entry -- with CUDA events on the batch
+ * the TMA-staged kernel with one or two float4 per thread or the register
+ * float4 kernel, times z splits aiming at 1..32 CTAs per SM, times 4096 /
+ * 16384 / 65536 cells per scalar-kernel entry when a simulation runs on the
+ * scalar kernel (nx % 4 != 0) -- with CUDA events on the batch
  * stream, restores the deposited state after every trial (it allocates a
  * temporary copy of one state set, freed before return), keeps the fastest
  * and stores its microseconds per step in *best_us (may be NULL).  No tally
