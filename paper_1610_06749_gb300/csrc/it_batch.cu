@@ -271,21 +271,26 @@ step_batched_vec_kernel(const BatchSim *__restrict__ sims, const VecEntry *__res
 // and nx <= 256: the batched counterpart of the single-context step kernel.
 // A CTA owns rows [y0, y0 + rows) of one simulation (full width) and planes
 // [z0, z1).  Every plane it needs (z0 - 1 .. z1) arrives by TMA in a ring of
-// shared-memory slots: a box of bt = min(256 / (nx/4), ny) rows per species
-// plus one halo row above and below, wrapped when the faces are periodic;
-// rows and planes outside the simulation's tensor arrive as zeros (the
-// absorbing faces and the electrode ghost planes).  Each simulation's
-// tensor maps (two sets x two species x main/halo box) sit in global memory.
-// The last warp to release a slot refills it with the plane S further on.
-// Thread t owns the float4 x-segment t mod (nx/4) of row t div (nx/4), keeps
-// planes k-1 and k of it in registers and reads x/y neighbours and plane k+1
-// from shared memory: the same per-cell operation sequence as every other
-// kernel.  Every ring wait is bounded (2^32 SM cycles); a wait that runs out
-// raises the error flag, and the CTA drains the copies it issued and returns.
+// shared-memory slots: a box of bt = min(256 IPT / (nx/4), 256, ny) rows per
+// species plus one halo row above and below, wrapped when the faces are
+// periodic; rows and planes outside the simulation's tensor arrive as zeros
+// (the absorbing faces and the electrode ghost planes).  Each simulation's
+// tensor maps (two sets x two species x {main box for IPT = 1, main box for
+// IPT = 2, halo row}) sit in global memory.  The last warp to release a slot
+// refills it with the plane S further on.  Thread t owns the IPT float4
+// x-segments q = t + 256 it (segment q mod (nx/4) of row q div (nx/4)),
+// keeps planes k-1 and k of them in registers and reads x/y neighbours and
+// plane k+1 from shared memory: the same per-cell operation sequence as
+// every other kernel.  IPT = 1 runs three CTAs per SM, IPT = 2 two with
+// larger rings; a plane's round through the CTA sets the time, and two
+// float4 per thread halve the rounds per cell.  Every ring wait is bounded
+// (2^32 SM cycles); a wait that runs out raises the error flag, and the CTA
+// drains the copies it issued and returns.
 constexpr int BT_MAX_S = 8;
 constexpr int BT_WARPS = 8;
-// dynamic shared memory of the TMA batched kernel: three CTAs per SM; the
-// ring gets whatever slots fit (3..8; a slot is at most 12 KiB at nx = 256)
+// dynamic shared memory of the TMA batched kernel with one float4 per thread:
+// three CTAs per SM; the ring gets whatever slots fit (3..8; a slot is at
+// most 12 KiB at nx = 256)
 constexpr int kBtSmem = 70 * 1024;
 constexpr int kBtSmemFloats = (kBtSmem - 128) / 4;
 // with two float4 per thread: two CTAs per SM, twice the rows per box
